@@ -1,0 +1,179 @@
+/* cpb.h — C ABI of libcpb: a barrier-tiled 2-D heat-diffusion stencil for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The stencil
+ * -----------
+ * Grid: ny rows x nx columns, row-major, x fastest; cell (i, j), 0 <= i < nx,
+ * 0 <= j < ny.  Neighbours W=(i-1,j), E=(i+1,j), S=(i,j-1), N=(i,j+1).
+ * One step of the explicit flux-form update with conductivity kappa and
+ * source s (hdt = 0.5f * dt; every operation rounded in FP32, in this order):
+ *     fW = (kc + kW) * (uW - c)      fE = (kc + kE) * (uE - c)
+ *     fS = (kc + kS) * (uS - c)      fN = (kc + kN) * (uN - c)
+ *     u' = c + (hdt * ((fW + fE) + (fS + fN)) + dt * s)
+ * Boundary CPB_DIRICHLET0: a neighbour outside the grid has u = 0 and
+ * kappa = kc (the boundary face conducts with 2 kc).  CPB_PERIODIC: wrap.
+ * The paper (CuPBoP, arXiv 2206.07896) contains no stencil: the update, its
+ * boundary rule and its rounding order are this library's definition.  The
+ * library built with --fmad=false (libcpb_nofma.so) reproduces that order
+ * bit for bit; the default build (libcpb.so) lets the compiler contract
+ * multiply-adds into FMAs.
+ *
+ * Launch model
+ * ------------
+ * Calls follow the CUDA launch model the paper executes on CPUs (Sec. II,
+ * Sec. IV "Push task queue"): the caller supplies launch geometry (grid,
+ * block, dynamic shared bytes) as in <<<grid, block, shm>>> and the fields of
+ * the paper's kernel structure (Listing 6); every call only enqueues work on
+ * the caller's stream and returns (asynchronous launch, Sec. III-C "Implicit
+ * barrier insertion": the caller synchronises before reading results on the
+ * host).  Errors are status codes, never exceptions.
+ *
+ * Memory
+ * ------
+ * All field pointers are device memory owned by the caller; the library never
+ * allocates or frees them.  Storage formats:
+ *   CPB_F32         u, kappa, s: float, nx*ny each.
+ *   CPB_BF16_KAHAN  u: one 32-bit word per cell, bits 0..15 = hi (bf16),
+ *                   bits 16..31 = cmp (bf16), value = (float)hi - (float)cmp;
+ *                   kappa, s: bf16 (uint16 bit patterns), nx*ny each.
+ *                   Each step computes v in FP32 from the effective values,
+ *                   then hi' = rn_bf16(v), cmp' = rn_bf16((float)hi' - v).
+ * Streams are CUDA stream handles (cudaStream_t); NULL is the legacy default
+ * stream.
+ *
+ * Validation happens before any launch: a failed check returns its code and
+ * enqueues nothing.  A CUDA error from an enqueue returns CPB_ERR_CUDA
+ * (details: cpb_last_error_detail()).
+ */
+#ifndef CPB_H
+#define CPB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cpb_stream_t; /* == cudaStream_t */
+
+typedef enum {
+  CPB_SUCCESS = 0,
+  CPB_ERR_INVALID_VALUE = 1,      /* bad size, null pointer, bad enum, in-place call   */
+  CPB_ERR_UNSUPPORTED_CONFIG = 2, /* launch geometry / dtype with no compiled variant  */
+  CPB_ERR_SHARED_MEM = 3,         /* shared_bytes below what the variant needs         */
+  CPB_ERR_LAUNCH = 4,             /* kernel launch rejected (geometry beyond limits)   */
+  CPB_ERR_TIMEOUT = 5,            /* a bounded device-side wait gave up                */
+  CPB_ERR_CUDA = 6,               /* any other CUDA runtime error                      */
+  CPB_ERR_WORKSPACE = 7           /* workspace missing or smaller than required        */
+} cpb_status;
+
+typedef enum { CPB_F32 = 0, CPB_BF16_KAHAN = 1 } cpb_dtype;
+typedef enum { CPB_DIRICHLET0 = 0, CPB_PERIODIC = 1 } cpb_boundary;
+
+typedef struct {
+  unsigned x, y, z;
+} cpb_dim3;
+
+/* Parameters of the streaming temporal-blocked kernel (the tuned path).
+ *   k               time steps fused per pass over HBM (temporal block depth), 1..8
+ *   chunk_rows      output rows per warp work item (>= 1)
+ *   warps_per_block warps per CTA (1..32)
+ *   variant         0 = register-streaming with 128-bit loads (only variant) */
+typedef struct {
+  int k;
+  int chunk_rows;
+  int warps_per_block;
+  int variant;
+} cpb_tuning;
+
+int cpb_version(void);
+const char* cpb_status_string(cpb_status status);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* cpb_last_error_detail(void);
+
+/* Device facts used for launch sizing (current device). */
+cpb_status cpb_device_info(int* sm_count, int* l2_bytes, int* smem_optin_bytes);
+
+/* Advance `steps` steps; the result is ALWAYS in u_out.
+ *
+ * u_in is read.  When scratch == NULL, u_in is also the ping-pong buffer and
+ * is clobbered (steps >= 2); when scratch != NULL (nx*ny cells of the storage
+ * format) u_in is left untouched.  u_in, u_out and scratch must not overlap.
+ * steps == 0 copies u_in to u_out.
+ *
+ * Geometry (the paper's <<<grid, block, shm>>>):
+ *  - block = {bx, by, 1} with 1 <= bx*by <= 1024: the tiled one-step kernel,
+ *    one thread per cell, a (bx+2)x(by+2) shared tile of u and of kappa, one
+ *    __syncthreads; grid must be {ceil(nx/bx), ceil(ny/by), 1} and
+ *    shared_bytes >= 2*(bx+2)*(by+2)*4.  CPB_F32 only.  One launch per step.
+ *  - block = {0, 0, 0}: the tuned streaming kernel (grid and shared_bytes are
+ *    ignored); its parameters come from cpb_set_tuning / cpb_autotune for
+ *    this (nx, ny, dtype, bc), else from the built-in default.
+ * dt > 0 and finite.  Alignment: 16-byte aligned fields with nx % 4 == 0 use
+ * 128-bit accesses; anything else uses the scalar-access path (same results). */
+cpb_status cpb_stencil_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                              int ny, int steps, float dt, cpb_boundary bc, cpb_dtype dtype,
+                              cpb_dim3 grid, cpb_dim3 block, size_t shared_bytes, void* scratch,
+                              cpb_stream_t stream);
+
+/* Same as cpb_stencil_launch with block = {0,0,0} but with explicit tuning. */
+cpb_status cpb_stencil_launch_tuned(void* u_in, void* u_out, const void* kappa, const void* src,
+                                    int nx, int ny, int steps, float dt, cpb_boundary bc,
+                                    cpb_dtype dtype, const cpb_tuning* tuning, void* scratch,
+                                    cpb_stream_t stream);
+
+/* Tuning cache (process-wide, keyed by nx, ny, dtype, bc). */
+cpb_status cpb_set_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, const cpb_tuning* t);
+cpb_status cpb_get_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_tuning* t);
+
+/* Time candidate tunings on the caller's buffers (u_a and u_b are
+ * clobbered; kappa, src read) for `steps` steps each, store the fastest in the
+ * cache and return it in *best.  Synchronises `stream`. */
+cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src, int nx, int ny,
+                        int steps, float dt, cpb_boundary bc, cpb_dtype dtype, cpb_stream_t stream,
+                        cpb_tuning* best);
+
+/* FP64 sum of the field (CPB_F32: sum of (double)u; CPB_BF16_KAHAN: sum of
+ * (double)hi - (double)cmp), written to *d_out (device pointer).  Two
+ * deterministic passes (per-block partials in `workspace`, then one block in
+ * a fixed order): the same input gives the same bits on the same device.
+ * workspace: device memory of at least cpb_heat_sum_workspace_bytes(). */
+size_t cpb_heat_sum_workspace_bytes(int nx, int ny);
+cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
+                        void* workspace, size_t ws_bytes, cpb_stream_t stream);
+
+/* BF16 conversions on the device (round to nearest even).
+ * cpb_bf16_round: out[i] = rn_bf16(x[i]) (bf16 bit patterns).
+ * cpb_bf16k_pack: state[i] = hi | cmp << 16 with hi = rn(u), cmp = rn(hi - u).
+ * cpb_bf16k_unpack: u[i] = (float)hi - (float)cmp. */
+cpb_status cpb_bf16_round(const float* x, uint16_t* out, long long n, cpb_stream_t stream);
+cpb_status cpb_bf16k_pack(const float* u, uint32_t* state, long long n, cpb_stream_t stream);
+cpb_status cpb_bf16k_unpack(const uint32_t* state, float* u, long long n, cpb_stream_t stream);
+
+/* End-to-end call on HOST buffers: copies u0, kappa, src in (pinned host
+ * memory gives asynchronous copies), runs `steps` steps on the tuned path,
+ * copies the result to u_out_host and synchronises `stream`.  d_workspace:
+ * device memory of at least cpb_host_workspace_bytes(nx, ny, dtype). */
+size_t cpb_host_workspace_bytes(int nx, int ny, cpb_dtype dtype);
+cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const void* src_host,
+                            void* u_out_host, int nx, int ny, int steps, float dt, cpb_boundary bc,
+                            cpb_dtype dtype, void* d_workspace, size_t ws_bytes,
+                            cpb_stream_t stream);
+
+/* CUDA graph of a whole multi-step run (the launch sequence captured once and
+ * replayed; Sec. VI of the paper measures launch + sync overhead of many
+ * launches).  The pointers are baked into the graph.  tuning == NULL uses the
+ * cached / default tuning. */
+typedef struct cpb_graph_s* cpb_graph_t;
+cpb_status cpb_graph_create(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                            int ny, int steps, float dt, cpb_boundary bc, cpb_dtype dtype,
+                            const cpb_tuning* tuning, void* scratch, cpb_graph_t* graph);
+cpb_status cpb_graph_launch(cpb_graph_t graph, cpb_stream_t stream);
+cpb_status cpb_graph_destroy(cpb_graph_t graph);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPB_H */

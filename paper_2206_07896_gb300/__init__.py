@@ -1,0 +1,280 @@
+"""Python binding of libcpb (ctypes), a barrier-tiled heat stencil for GB300.
+
+The functions named ``cpb_*`` mirror the C ABI in ``include/cpb.h`` one to one:
+they only marshal arguments (torch tensors or integer device addresses,
+streams) and turn a non-success status into :class:`CpbError`.  Every step of
+the computation runs in the CUDA kernels of the shared library; there is no
+CPU path.  If the library has not been built the first call raises.
+
+Two builds are available: ``lib()`` (default, FMA contraction allowed) and
+``lib(fma=False)`` (``--fmad=false``: the library's FP32 rounding order bit for
+bit).  Module-level ``cpb_*`` functions use the default build; pass
+``library=lib(fma=False)`` or call the methods of that object for the other.
+
+Higher-level helpers: :func:`stencil` (allocating wrapper) and
+:class:`StencilFn` (autograd), both built from the ``cpb_*`` calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+CPB_SUCCESS = 0
+CPB_ERR_INVALID_VALUE = 1
+CPB_ERR_UNSUPPORTED_CONFIG = 2
+CPB_ERR_SHARED_MEM = 3
+CPB_ERR_LAUNCH = 4
+CPB_ERR_TIMEOUT = 5
+CPB_ERR_CUDA = 6
+CPB_ERR_WORKSPACE = 7
+
+CPB_F32 = 0
+CPB_BF16_KAHAN = 1
+CPB_DIRICHLET0 = 0
+CPB_PERIODIC = 1
+
+
+class CpbError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{func}: status {status}" + (f" ({detail})" if detail else ""))
+
+
+class cpb_dim3(C.Structure):
+    _fields_ = [("x", C.c_uint), ("y", C.c_uint), ("z", C.c_uint)]
+
+
+class cpb_tuning(C.Structure):
+    _fields_ = [("k", C.c_int), ("chunk_rows", C.c_int), ("warps_per_block", C.c_int),
+                ("variant", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp, _i, _f, _sz, _ll = C.c_void_p, C.c_int, C.c_float, C.c_size_t, C.c_longlong
+
+# name -> (restype, argtypes); mirrors include/cpb.h
+_SIGS = {
+    "cpb_version": (_i, []),
+    "cpb_status_string": (C.c_char_p, [_i]),
+    "cpb_last_error_detail": (C.c_char_p, []),
+    "cpb_device_info": (_i, [C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
+    "cpb_stencil_launch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, cpb_dim3, cpb_dim3, _sz,
+                                _vp, _vp]),
+    "cpb_stencil_launch_tuned": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i,
+                                      C.POINTER(cpb_tuning), _vp, _vp]),
+    "cpb_set_tuning": (_i, [_i, _i, _i, _i, C.POINTER(cpb_tuning)]),
+    "cpb_get_tuning": (_i, [_i, _i, _i, _i, C.POINTER(cpb_tuning)]),
+    "cpb_autotune": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, C.POINTER(cpb_tuning)]),
+    "cpb_heat_sum_workspace_bytes": (_sz, [_i, _i]),
+    "cpb_heat_sum": (_i, [_vp, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "cpb_bf16_round": (_i, [_vp, _vp, _ll, _vp]),
+    "cpb_bf16k_pack": (_i, [_vp, _vp, _ll, _vp]),
+    "cpb_bf16k_unpack": (_i, [_vp, _vp, _ll, _vp]),
+    "cpb_host_workspace_bytes": (_sz, [_i, _i, _i]),
+    "cpb_stencil_host": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _sz, _vp]),
+    "cpb_graph_create": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, C.POINTER(cpb_tuning),
+                              _vp, C.POINTER(_vp)]),
+    "cpb_graph_launch": (_i, [_vp, _vp]),
+    "cpb_graph_destroy": (_i, [_vp]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def ptr(x) -> int | None:
+    """Device address of a torch tensor, or an int / None passed through."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def host_ptr(x) -> int | None:
+    """Host address of a numpy array or pinned torch CPU tensor."""
+    if x is None:
+        return None
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    return int(x.data_ptr())
+
+
+def stream_handle(stream=None) -> int | None:
+    """cudaStream_t of a torch stream (default: torch's current stream)."""
+    if isinstance(stream, int):
+        return stream
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dim3(v) -> cpb_dim3:
+    if isinstance(v, cpb_dim3):
+        return v
+    v = tuple(v) + (1,) * (3 - len(tuple(v))) if len(tuple(v)) < 3 else tuple(v)
+    return cpb_dim3(*[int(a) for a in v])
+
+
+class Library:
+    """One loaded build of libcpb; methods mirror the C ABI."""
+
+    def __init__(self, path: str):
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcpb is not built ({path} missing): run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        self.path = path
+        self._lib = C.CDLL(path, mode=C.RTLD_LOCAL)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(self._lib, name)
+            fn.restype = res
+            fn.argtypes = args
+
+    def _call(self, name, *args):
+        st = getattr(self._lib, name)(*args)
+        if st != CPB_SUCCESS:
+            detail = self._lib.cpb_last_error_detail().decode()
+            raise CpbError(st, name, detail or self._lib.cpb_status_string(st).decode())
+        return st
+
+    # -- C ABI mirrors -----------------------------------------------------
+    def cpb_version(self) -> int:
+        return self._lib.cpb_version()
+
+    def cpb_status_string(self, status: int) -> str:
+        return self._lib.cpb_status_string(status).decode()
+
+    def cpb_last_error_detail(self) -> str:
+        return self._lib.cpb_last_error_detail().decode()
+
+    def cpb_device_info(self):
+        a, b, c = _i(), _i(), _i()
+        self._call("cpb_device_info", C.byref(a), C.byref(b), C.byref(c))
+        return {"sm_count": a.value, "l2_bytes": b.value, "smem_optin_bytes": c.value}
+
+    def cpb_stencil_launch(self, u_in, u_out, kappa, src, nx, ny, steps, dt, bc, dtype, grid,
+                           block, shared_bytes, scratch=None, stream=None):
+        self._call("cpb_stencil_launch", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny, steps,
+                   float(dt), bc, dtype, _dim3(grid), _dim3(block), shared_bytes, ptr(scratch),
+                   stream_handle(stream))
+
+    def cpb_stencil_launch_tuned(self, u_in, u_out, kappa, src, nx, ny, steps, dt, bc, dtype,
+                                 tuning=None, scratch=None, stream=None):
+        t = C.byref(as_tuning(tuning)) if tuning is not None else None
+        self._call("cpb_stencil_launch_tuned", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny,
+                   steps, float(dt), bc, dtype, t, ptr(scratch), stream_handle(stream))
+
+    def cpb_set_tuning(self, nx, ny, dtype, bc, tuning):
+        self._call("cpb_set_tuning", nx, ny, dtype, bc, C.byref(as_tuning(tuning)))
+
+    def cpb_get_tuning(self, nx, ny, dtype, bc) -> dict:
+        t = cpb_tuning()
+        self._call("cpb_get_tuning", nx, ny, dtype, bc, C.byref(t))
+        return t.as_dict()
+
+    def cpb_autotune(self, u_a, u_b, kappa, src, nx, ny, steps, dt, bc, dtype, stream=None) -> dict:
+        t = cpb_tuning()
+        self._call("cpb_autotune", ptr(u_a), ptr(u_b), ptr(kappa), ptr(src), nx, ny, steps, float(dt),
+                   bc, dtype, stream_handle(stream), C.byref(t))
+        return t.as_dict()
+
+    def cpb_heat_sum_workspace_bytes(self, nx, ny) -> int:
+        return self._lib.cpb_heat_sum_workspace_bytes(nx, ny)
+
+    def cpb_heat_sum(self, u, nx, ny, dtype, d_out, workspace, ws_bytes, stream=None):
+        self._call("cpb_heat_sum", ptr(u), nx, ny, dtype, ptr(d_out), ptr(workspace), ws_bytes,
+                   stream_handle(stream))
+
+    def cpb_bf16_round(self, x, out, n, stream=None):
+        self._call("cpb_bf16_round", ptr(x), ptr(out), n, stream_handle(stream))
+
+    def cpb_bf16k_pack(self, u, state, n, stream=None):
+        self._call("cpb_bf16k_pack", ptr(u), ptr(state), n, stream_handle(stream))
+
+    def cpb_bf16k_unpack(self, state, u, n, stream=None):
+        self._call("cpb_bf16k_unpack", ptr(state), ptr(u), n, stream_handle(stream))
+
+    def cpb_host_workspace_bytes(self, nx, ny, dtype) -> int:
+        return self._lib.cpb_host_workspace_bytes(nx, ny, dtype)
+
+    def cpb_stencil_host(self, u0_host, kappa_host, src_host, u_out_host, nx, ny, steps, dt, bc,
+                         dtype, d_workspace, ws_bytes, stream=None):
+        self._call("cpb_stencil_host", host_ptr(u0_host), host_ptr(kappa_host), host_ptr(src_host),
+                   host_ptr(u_out_host), nx, ny, steps, float(dt), bc, dtype, ptr(d_workspace),
+                   ws_bytes, stream_handle(stream))
+
+    def cpb_graph_create(self, u_in, u_out, kappa, src, nx, ny, steps, dt, bc, dtype, tuning=None,
+                         scratch=None) -> int:
+        g = _vp()
+        t = C.byref(as_tuning(tuning)) if tuning is not None else None
+        self._call("cpb_graph_create", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny, steps,
+                   float(dt), bc, dtype, t, ptr(scratch), C.byref(g))
+        return g.value
+
+    def cpb_graph_launch(self, graph, stream=None):
+        self._call("cpb_graph_launch", graph, stream_handle(stream))
+
+    def cpb_graph_destroy(self, graph):
+        self._call("cpb_graph_destroy", graph)
+
+
+def as_tuning(t) -> cpb_tuning:
+    if isinstance(t, cpb_tuning):
+        return t
+    if isinstance(t, dict):
+        return cpb_tuning(int(t["k"]), int(t["chunk_rows"]), int(t.get("warps_per_block", 4)),
+                          int(t.get("variant", 0)))
+    return cpb_tuning(*[int(v) for v in t])
+
+
+_LIBS: dict[bool, Library] = {}
+
+
+def lib(fma: bool = True) -> Library:
+    """The default build (fma=True) or the --fmad=false build."""
+    if fma not in _LIBS:
+        _LIBS[fma] = Library(_build.lib_path("libcpb.so" if fma else "libcpb_nofma.so"))
+    return _LIBS[fma]
+
+
+def _forward(name):
+    def f(*args, library: Library | None = None, **kw):
+        return getattr(library or lib(), name)(*args, **kw)
+    f.__name__ = name
+    f.__doc__ = f"Module-level {name} on the default build (see include/cpb.h)."
+    return f
+
+
+for _n in _SIGS:
+    globals()[_n] = _forward(_n)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrappers built on the C ABI (torch for memory and streams only)
+# ---------------------------------------------------------------------------
+def stencil(u, kappa, src, steps, dt, bc=CPB_DIRICHLET0, dtype=CPB_F32, tuning=None,
+            library: Library | None = None, stream=None):
+    """Return a new tensor holding `steps` steps applied to u (u is not modified)."""
+    import torch
+    out = torch.empty_like(u)
+    scratch = torch.empty_like(u) if steps >= 2 else None
+    ny, nx = u.shape[0], u.shape[1]
+    (library or lib()).cpb_stencil_launch_tuned(u, out, kappa, src, nx, ny, steps, dt, bc, dtype,
+                                                tuning=tuning, scratch=scratch, stream=stream)
+    return out
+
+
+def heat_sum(u, dtype=CPB_F32, library: Library | None = None, stream=None):
+    """FP64 heat sum of a device field; returns a 0-d float64 CUDA tensor."""
+    import torch
+    L = library or lib()
+    ny, nx = u.shape[0], u.shape[1]
+    ws_bytes = L.cpb_heat_sum_workspace_bytes(nx, ny)
+    ws = torch.empty(max(ws_bytes, 8) // 8, dtype=torch.float64, device=u.device)
+    out = torch.empty((), dtype=torch.float64, device=u.device)
+    L.cpb_heat_sum(u, nx, ny, dtype, out, ws, ws_bytes, stream=stream)
+    return out

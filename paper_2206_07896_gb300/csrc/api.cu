@@ -1,0 +1,476 @@
+// libcpb C ABI: validation, pass scheduling, tuning cache, autotuner, heat
+// sum, BF16 conversions, host end-to-end call and CUDA-graph capture.
+//
+// A launch call is the host half of the paper's launch model (Sec. IV, "Push
+// task queue"): it checks the arguments, decides the sequence of kernel
+// passes, enqueues them on the caller's stream and returns without waiting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace cpb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cpb_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return CPB_SUCCESS;
+  g_last_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorInvalidConfiguration || e == cudaErrorLaunchOutOfResources)
+    return CPB_ERR_LAUNCH;
+  return CPB_ERR_CUDA;
+}
+
+#define CPB_TRY(expr)                            \
+  do {                                           \
+    cpb_status _st = from_cuda(expr);            \
+    if (_st != CPB_SUCCESS) return _st;          \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+size_t u_bytes(cpb_dtype d) { return 4; }                    // f32 or (hi, cmp) word
+size_t ks_bytes(cpb_dtype d) { return d == CPB_F32 ? 4 : 2; }  // kappa / source element
+
+bool overlap(const void* a, const void* b, size_t n) {
+  if (!a || !b) return false;
+  uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + n && y < x + n;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  return sms > 0 ? sms : 148;
+}
+
+// ---------------------------------------------------------------------------
+// Tuning cache
+// ---------------------------------------------------------------------------
+using TuneKey = std::tuple<int, int, int, int>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, cpb_tuning> g_tune;
+
+bool tuning_valid(const cpb_tuning& t) {
+  return t.k >= 1 && t.k <= 8 && t.chunk_rows >= 1 && t.warps_per_block >= 1 &&
+         t.warps_per_block <= 8 && t.variant == 0;
+}
+
+// Built-in default: depth 4, and chunks sized so the grid yields about 16
+// warp items per SM (one resident wave at the kernel's register footprint).
+cpb_tuning default_tuning(int nx, int ny, cpb_dtype) {
+  cpb_tuning t;
+  t.k = 4;
+  t.warps_per_block = 4;
+  t.variant = 0;
+  const long long strips = (nx + strip_out_width(t.k) - 1) / strip_out_width(t.k);
+  const long long target = (long long)device_sm_count() * 12;
+  long long rows = (strips * ny + target - 1) / target;
+  t.chunk_rows = (int)std::max(16LL, std::min(rows, 1024LL));
+  return t;
+}
+
+cpb_tuning lookup_tuning(int nx, int ny, cpb_dtype d, cpb_boundary bc) {
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  auto it = g_tune.find(TuneKey(nx, ny, (int)d, (int)bc));
+  if (it != g_tune.end()) return it->second;
+  return default_tuning(nx, ny, d);
+}
+
+// ---------------------------------------------------------------------------
+// Pass schedule
+// ---------------------------------------------------------------------------
+// Depths of the passes for `steps` steps at depth k.  Without scratch the
+// passes alternate u_in -> u_out -> u_in ..., so the result lands in u_out
+// only for an odd number of passes: an even count is made odd by splitting a
+// pass of depth >= 2 in two; if every pass has depth 1, the result is copied
+// from u_in at the end (*copy_at_end).
+std::vector<int> pass_depths(int steps, int k, bool have_scratch, bool* copy_at_end) {
+  std::vector<int> d(steps / k, k);
+  if (steps % k) d.push_back(steps % k);
+  *copy_at_end = false;
+  if (!have_scratch && d.size() % 2 == 0 && !d.empty()) {
+    int idx = -1;
+    for (int i = (int)d.size() - 1; i >= 0; --i)
+      if (d[i] >= 2) {
+        idx = i;
+        break;
+      }
+    if (idx >= 0) {
+      int a = d[idx] - d[idx] / 2, b = d[idx] / 2;
+      d[idx] = a;
+      d.insert(d.begin() + idx + 1, b);
+    } else {
+      *copy_at_end = true;
+    }
+  }
+  return d;
+}
+
+struct Fields {
+  void* u_in;
+  void* u_out;
+  const void* kappa;
+  const void* src;
+  void* scratch;
+};
+
+cpb_status check_common(const Fields& f, int nx, int ny, int steps, float dt, cpb_boundary bc,
+                        cpb_dtype dtype) {
+  if (nx < 1 || ny < 1 || steps < 0) return CPB_ERR_INVALID_VALUE;
+  if (!(dt > 0.0f) || !std::isfinite(dt)) return CPB_ERR_INVALID_VALUE;
+  if (bc != CPB_DIRICHLET0 && bc != CPB_PERIODIC) return CPB_ERR_INVALID_VALUE;
+  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  if (!f.u_in || !f.u_out || !f.kappa) return CPB_ERR_INVALID_VALUE;
+  const size_t n = (size_t)nx * (size_t)ny;
+  if (n > (size_t)1 << 40) return CPB_ERR_INVALID_VALUE;
+  const size_t ub = n * u_bytes(dtype);
+  if (overlap(f.u_in, f.u_out, ub) || overlap(f.u_in, f.scratch, ub) ||
+      overlap(f.u_out, f.scratch, ub))
+    return CPB_ERR_INVALID_VALUE;
+  const size_t ua = u_bytes(dtype), ka = ks_bytes(dtype);
+  if (!aligned(f.u_in, ua) || !aligned(f.u_out, ua) || !aligned(f.scratch, ua) ||
+      !aligned(f.kappa, ka) || !aligned(f.src, ka))
+    return CPB_ERR_INVALID_VALUE;
+  return CPB_SUCCESS;
+}
+
+cpb_status enqueue_tuned(const Fields& f, int nx, int ny, int steps, float dt, cpb_boundary bc,
+                         cpb_dtype dtype, const cpb_tuning& t, cudaStream_t s) {
+  const size_t ub = (size_t)nx * ny * u_bytes(dtype);
+  if (steps == 0) {
+    CPB_TRY(cudaMemcpyAsync(f.u_out, f.u_in, ub, cudaMemcpyDeviceToDevice, s));
+    return CPB_SUCCESS;
+  }
+  const int ow = strip_out_width(t.k);
+  const long long items = (long long)((nx + ow - 1) / ow) * ((ny + t.chunk_rows - 1) / t.chunk_rows);
+  if ((items + t.warps_per_block - 1) / t.warps_per_block > 0x7fffffffLL) return CPB_ERR_LAUNCH;
+
+  const size_t ka = dtype == CPB_F32 ? 16 : 8;
+  StreamPass p;
+  p.kappa = f.kappa;
+  p.src = f.src;
+  p.nx = nx;
+  p.ny = ny;
+  p.dt = dt;
+  p.hdt = 0.5f * dt;
+  p.bc = (int)bc;
+  p.vec = (nx % 4 == 0) && aligned(f.u_in, 16) && aligned(f.u_out, 16) && aligned(f.scratch, 16) &&
+          aligned(f.kappa, ka) && aligned(f.src, ka);
+  p.chunk_rows = t.chunk_rows;
+  p.warps_per_block = t.warps_per_block;
+
+  bool copy_at_end = false;
+  std::vector<int> depths = pass_depths(steps, t.k, f.scratch != nullptr, &copy_at_end);
+  const int P = (int)depths.size();
+  const void* src_buf = f.u_in;
+  void* dst = nullptr;
+  for (int i = 0; i < P; ++i) {
+    if (f.scratch)
+      dst = ((P - 1 - i) % 2 == 0) ? f.u_out : f.scratch;
+    else if (!copy_at_end)
+      dst = ((P - 1 - i) % 2 == 0) ? f.u_out : f.u_in;
+    else
+      dst = (i % 2 == 0) ? f.u_out : f.u_in;
+    p.u_in = src_buf;
+    p.u_out = dst;
+    cudaError_t e = dtype == CPB_F32 ? launch_stream_f32(p, depths[i], s)
+                                     : launch_stream_bf16k(p, depths[i], s);
+    CPB_TRY(e);
+    src_buf = dst;
+  }
+  if (copy_at_end) CPB_TRY(cudaMemcpyAsync(f.u_out, f.u_in, ub, cudaMemcpyDeviceToDevice, s));
+  return CPB_SUCCESS;
+}
+
+cpb_status enqueue_tile(const Fields& f, int nx, int ny, int steps, float dt, cpb_boundary bc,
+                        cpb_dim3 grid, cpb_dim3 block, size_t shared_bytes, cudaStream_t s) {
+  const long long bx = block.x, by = block.y;
+  if (block.z != 1 || bx < 1 || by < 1 || bx * by > 1024) return CPB_ERR_UNSUPPORTED_CONFIG;
+  if ((long long)grid.x != (nx + bx - 1) / bx || (long long)grid.y != (ny + by - 1) / by || grid.z != 1)
+    return CPB_ERR_INVALID_VALUE;
+  const size_t need = 2 * sizeof(float) * (size_t)(bx + 2) * (size_t)(by + 2);
+  if (shared_bytes < need) return CPB_ERR_SHARED_MEM;
+  const size_t ub = (size_t)nx * ny * sizeof(float);
+  if (steps == 0) {
+    CPB_TRY(cudaMemcpyAsync(f.u_out, f.u_in, ub, cudaMemcpyDeviceToDevice, s));
+    return CPB_SUCCESS;
+  }
+  bool copy_at_end = false;
+  std::vector<int> depths = pass_depths(steps, 1, f.scratch != nullptr, &copy_at_end);
+  const int P = (int)depths.size();
+  const void* src_buf = f.u_in;
+  for (int i = 0; i < P; ++i) {
+    void* dst;
+    if (f.scratch)
+      dst = ((P - 1 - i) % 2 == 0) ? f.u_out : f.scratch;
+    else if (!copy_at_end)
+      dst = ((P - 1 - i) % 2 == 0) ? f.u_out : f.u_in;
+    else
+      dst = (i % 2 == 0) ? f.u_out : f.u_in;
+    CPB_TRY(launch_tile_f32(static_cast<const float*>(src_buf), static_cast<float*>(dst),
+                            static_cast<const float*>(f.kappa), static_cast<const float*>(f.src),
+                            nx, ny, dt, (int)bc, dim3(grid.x, grid.y, 1), dim3(block.x, block.y, 1),
+                            need, s));
+    src_buf = dst;
+  }
+  if (copy_at_end) CPB_TRY(cudaMemcpyAsync(f.u_out, f.u_in, ub, cudaMemcpyDeviceToDevice, s));
+  return CPB_SUCCESS;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct cpb_graph_s {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+int cpb_version(void) { return 1; }
+
+const char* cpb_status_string(cpb_status st) {
+  switch (st) {
+    case CPB_SUCCESS: return "success";
+    case CPB_ERR_INVALID_VALUE: return "invalid value";
+    case CPB_ERR_UNSUPPORTED_CONFIG: return "unsupported configuration";
+    case CPB_ERR_SHARED_MEM: return "shared memory too small";
+    case CPB_ERR_LAUNCH: return "launch failed";
+    case CPB_ERR_TIMEOUT: return "device wait timed out";
+    case CPB_ERR_CUDA: return "CUDA error";
+    case CPB_ERR_WORKSPACE: return "workspace missing or too small";
+  }
+  return "unknown status";
+}
+
+const char* cpb_last_error_detail(void) { return g_last_error.c_str(); }
+
+cpb_status cpb_device_info(int* sm_count, int* l2_bytes, int* smem_optin_bytes) {
+  int dev = 0;
+  CPB_TRY(cudaGetDevice(&dev));
+  if (sm_count) CPB_TRY(cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev));
+  if (l2_bytes) CPB_TRY(cudaDeviceGetAttribute(l2_bytes, cudaDevAttrL2CacheSize, dev));
+  if (smem_optin_bytes)
+    CPB_TRY(cudaDeviceGetAttribute(smem_optin_bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_stencil_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                              int ny, int steps, float dt, cpb_boundary bc, cpb_dtype dtype,
+                              cpb_dim3 grid, cpb_dim3 block, size_t shared_bytes, void* scratch,
+                              cpb_stream_t stream) {
+  Fields f{u_in, u_out, kappa, src, scratch};
+  cpb_status st = check_common(f, nx, ny, steps, dt, bc, dtype);
+  if (st != CPB_SUCCESS) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (block.x == 0 && block.y == 0 && block.z == 0)
+    return enqueue_tuned(f, nx, ny, steps, dt, bc, dtype, lookup_tuning(nx, ny, dtype, bc), s);
+  if (dtype != CPB_F32) return CPB_ERR_UNSUPPORTED_CONFIG;
+  if (!src) return CPB_ERR_INVALID_VALUE;
+  return enqueue_tile(f, nx, ny, steps, dt, bc, grid, block, shared_bytes, s);
+}
+
+cpb_status cpb_stencil_launch_tuned(void* u_in, void* u_out, const void* kappa, const void* src,
+                                    int nx, int ny, int steps, float dt, cpb_boundary bc,
+                                    cpb_dtype dtype, const cpb_tuning* tuning, void* scratch,
+                                    cpb_stream_t stream) {
+  Fields f{u_in, u_out, kappa, src, scratch};
+  cpb_status st = check_common(f, nx, ny, steps, dt, bc, dtype);
+  if (st != CPB_SUCCESS) return st;
+  cpb_tuning t = tuning ? *tuning : lookup_tuning(nx, ny, dtype, bc);
+  if (!tuning_valid(t)) return CPB_ERR_UNSUPPORTED_CONFIG;
+  return enqueue_tuned(f, nx, ny, steps, dt, bc, dtype, t, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cpb_status cpb_set_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, const cpb_tuning* t) {
+  if (!t || !tuning_valid(*t) || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune[TuneKey(nx, ny, (int)dtype, (int)bc)] = *t;
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_get_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_tuning* t) {
+  if (!t || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  *t = lookup_tuning(nx, ny, dtype, bc);
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src, int nx, int ny,
+                        int steps, float dt, cpb_boundary bc, cpb_dtype dtype, cpb_stream_t stream,
+                        cpb_tuning* best) {
+  Fields f{u_a, u_b, kappa, src, nullptr};
+  cpb_status st = check_common(f, nx, ny, steps < 1 ? 1 : steps, dt, bc, dtype);
+  if (st != CPB_SUCCESS) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int ks[] = {1, 2, 3, 4, 5, 6, 8};
+  const int chunks[] = {32, 64, 128, 256, 512};
+  const int wpbs[] = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  CPB_TRY(cudaEventCreate(&e0));
+  CPB_TRY(cudaEventCreate(&e1));
+  float best_rate = -1.0f;
+  cpb_tuning bt = default_tuning(nx, ny, dtype);
+  const int probe = steps >= 1 ? steps : 16;
+  for (int k : ks)
+    for (int c : chunks)
+      for (int w : wpbs) {
+        if (c > 2 * ny && c != chunks[0]) continue;
+        cpb_tuning t{k, c, w, 0};
+        // Probe length: a multiple of k near `probe` so every pass has depth k.
+        int n = std::max(k, (probe / k) * k);
+        cpb_status r = enqueue_tuned(f, nx, ny, n, dt, bc, dtype, t, s);  // warm-up
+        if (r != CPB_SUCCESS) continue;
+        CPB_TRY(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 2; ++rep) enqueue_tuned(f, nx, ny, n, dt, bc, dtype, t, s);
+        CPB_TRY(cudaEventRecord(e1, s));
+        CPB_TRY(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CPB_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        float rate = (float)(2.0 * n * (double)nx * ny / (ms * 1e-3));
+        if (ms > 0 && rate > best_rate) {
+          best_rate = rate;
+          bt = t;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CPB_TRY(cudaGetLastError());
+  cpb_set_tuning(nx, ny, dtype, bc, &bt);
+  if (best) *best = bt;
+  return CPB_SUCCESS;
+}
+
+size_t cpb_heat_sum_workspace_bytes(int nx, int ny) {
+  if (nx < 1 || ny < 1) return 0;
+  return sizeof(double) * (size_t)heat_sum_blocks((long long)nx * ny);
+}
+
+cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
+                        void* workspace, size_t ws_bytes, cpb_stream_t stream) {
+  if (!u || !d_out || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  if (!aligned(u, 4) || !aligned(d_out, 8)) return CPB_ERR_INVALID_VALUE;
+  const long long n = (long long)nx * ny;
+  const int nb = heat_sum_blocks(n);
+  if (!workspace || !aligned(workspace, 8) || ws_bytes < sizeof(double) * (size_t)nb)
+    return CPB_ERR_WORKSPACE;
+  return from_cuda(launch_heat_sum(u, n, (int)dtype, d_out, static_cast<double*>(workspace), nb,
+                                   reinterpret_cast<cudaStream_t>(stream)));
+}
+
+cpb_status cpb_bf16_round(const float* x, uint16_t* out, long long n, cpb_stream_t stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return CPB_ERR_INVALID_VALUE;
+  if (n == 0) return CPB_SUCCESS;
+  return from_cuda(launch_bf16_round(x, out, n, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+cpb_status cpb_bf16k_pack(const float* u, uint32_t* state, long long n, cpb_stream_t stream) {
+  if (n < 0 || (n > 0 && (!u || !state))) return CPB_ERR_INVALID_VALUE;
+  if (n == 0) return CPB_SUCCESS;
+  return from_cuda(launch_bf16k_pack(u, state, n, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+cpb_status cpb_bf16k_unpack(const uint32_t* state, float* u, long long n, cpb_stream_t stream) {
+  if (n < 0 || (n > 0 && (!u || !state))) return CPB_ERR_INVALID_VALUE;
+  if (n == 0) return CPB_SUCCESS;
+  return from_cuda(launch_bf16k_unpack(state, u, n, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t cpb_host_workspace_bytes(int nx, int ny, cpb_dtype dtype) {
+  if (nx < 1 || ny < 1) return 0;
+  const size_t n = (size_t)nx * ny;
+  return 2 * align256(n * u_bytes(dtype)) + 2 * align256(n * ks_bytes(dtype));
+}
+
+cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const void* src_host,
+                            void* u_out_host, int nx, int ny, int steps, float dt, cpb_boundary bc,
+                            cpb_dtype dtype, void* d_workspace, size_t ws_bytes,
+                            cpb_stream_t stream) {
+  if (!u0_host || !kappa_host || !u_out_host || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  const size_t need = cpb_host_workspace_bytes(nx, ny, dtype);
+  if (!d_workspace || ws_bytes < need || !aligned(d_workspace, 256)) return CPB_ERR_WORKSPACE;
+  const size_t n = (size_t)nx * ny;
+  const size_t ub = n * u_bytes(dtype), kb = n * ks_bytes(dtype);
+  char* base = static_cast<char*>(d_workspace);
+  void* ua = base;
+  void* ubuf = base + align256(ub);
+  void* kd = base + 2 * align256(ub);
+  void* sd = src_host ? base + 2 * align256(ub) + align256(kb) : nullptr;
+  Fields f{ua, ubuf, kd, sd, nullptr};
+  cpb_status st = check_common(f, nx, ny, steps, dt, bc, dtype);
+  if (st != CPB_SUCCESS) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CPB_TRY(cudaMemcpyAsync(ua, u0_host, ub, cudaMemcpyHostToDevice, s));
+  CPB_TRY(cudaMemcpyAsync(kd, kappa_host, kb, cudaMemcpyHostToDevice, s));
+  if (sd) CPB_TRY(cudaMemcpyAsync(sd, src_host, kb, cudaMemcpyHostToDevice, s));
+  st = enqueue_tuned(f, nx, ny, steps, dt, bc, dtype, lookup_tuning(nx, ny, dtype, bc), s);
+  if (st != CPB_SUCCESS) return st;
+  CPB_TRY(cudaMemcpyAsync(u_out_host, ubuf, ub, cudaMemcpyDeviceToHost, s));
+  CPB_TRY(cudaStreamSynchronize(s));
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_graph_create(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                            int ny, int steps, float dt, cpb_boundary bc, cpb_dtype dtype,
+                            const cpb_tuning* tuning, void* scratch, cpb_graph_t* graph) {
+  if (!graph) return CPB_ERR_INVALID_VALUE;
+  *graph = nullptr;
+  Fields f{u_in, u_out, kappa, src, scratch};
+  cpb_status st = check_common(f, nx, ny, steps, dt, bc, dtype);
+  if (st != CPB_SUCCESS) return st;
+  cpb_tuning t = tuning ? *tuning : lookup_tuning(nx, ny, dtype, bc);
+  if (!tuning_valid(t)) return CPB_ERR_UNSUPPORTED_CONFIG;
+  cudaStream_t cs;
+  CPB_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = enqueue_tuned(f, nx, ny, steps, dt, bc, dtype, t, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  cudaStreamDestroy(cs);
+  if (st != CPB_SUCCESS) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  CPB_TRY(e);
+  cudaGraphExec_t ex;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return from_cuda(e);
+  }
+  cpb_graph_s* h = new cpb_graph_s{g, ex};
+  *graph = h;
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_graph_launch(cpb_graph_t graph, cpb_stream_t stream) {
+  if (!graph) return CPB_ERR_INVALID_VALUE;
+  return from_cuda(cudaGraphLaunch(graph->exec, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+cpb_status cpb_graph_destroy(cpb_graph_t graph) {
+  if (!graph) return CPB_ERR_INVALID_VALUE;
+  cudaGraphExecDestroy(graph->exec);
+  cudaGraphDestroy(graph->graph);
+  delete graph;
+  return CPB_SUCCESS;
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// Device-side building blocks shared by the stencil kernels of libcpb.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cpb.h"
+
+namespace cpb {
+
+enum { BC_DIRICHLET = 0, BC_PERIODIC = 1 };
+
+// One step of the canonical flux-form update for one cell, from precomputed
+// face conductivity sums (kc + kn) and the precomputed source increment
+// dt * s.  Both are time-invariant and their values are identical to forming
+// them inline, so the rounding sequence is exactly
+//   c + (hdt * (((kc+kW)*(uW-c) + (kc+kE)*(uE-c)) + ((kc+kS)*(uS-c) + (kc+kN)*(uN-c))) + dt*s).
+__device__ __forceinline__ float cell_update(float c, float uW, float uE, float uS, float uN,
+                                             float fkW, float fkE, float fkS, float fkN, float dts,
+                                             float hdt) {
+  float fW = fkW * (uW - c);
+  float fE = fkE * (uE - c);
+  float fS = fkS * (uS - c);
+  float fN = fkN * (uN - c);
+  float acc = (fW + fE) + (fS + fN);
+  return c + (hdt * acc + dts);
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ int clamp_index(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// BF16-Kahan state word: bits 0..15 hi, bits 16..31 cmp.
+__device__ __forceinline__ float bf16_bits_to_f32(uint32_t h16) {
+  return __uint_as_float(h16 << 16);
+}
+
+__device__ __forceinline__ float kahan_value(uint32_t w) {
+  return bf16_bits_to_f32(w & 0xffffu) - bf16_bits_to_f32(w >> 16);
+}
+
+__device__ __forceinline__ uint32_t f32_to_bf16_bits(float v) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// Round an FP32 step result into BF16-Kahan storage; returns the packed word
+// and (through eff) the effective value the stored state represents.
+__device__ __forceinline__ uint32_t kahan_round(float v, float& eff) {
+  uint32_t hi = f32_to_bf16_bits(v);
+  float hif = bf16_bits_to_f32(hi);
+  uint32_t cm = f32_to_bf16_bits(hif - v);
+  eff = hif - bf16_bits_to_f32(cm);
+  return hi | (cm << 16);
+}
+
+}  // namespace cpb

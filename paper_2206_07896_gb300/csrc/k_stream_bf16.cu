@@ -1,0 +1,8 @@
+// BF16-Kahan-storage instantiations of the streaming temporal-blocked kernel.
+#include "k_stream.cuh"
+
+namespace cpb {
+cudaError_t launch_stream_bf16k(const StreamPass& p, int k, cudaStream_t s) {
+  return launch_stream_any<true>(p, k, s);
+}
+}  // namespace cpb
