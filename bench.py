@@ -1,0 +1,363 @@
+"""Benchmark: Gcell-updates/s and fraction of the HBM roofline on one GB300.
+
+Headline workload (one bench step): the plain FP32 stencil at scale -- one
+8192 x 8192 grid, lognormal conductivity, periodic boundary, 1000 time steps
+at the autotuned temporal-block depth -- followed by the FP64 heat sum of the
+result.  Inputs (4 x 256 MiB) are larger than L2 and resident in HBM when the
+timed region starts.  The other forms of the path (BF16-Kahan storage at
+16384^2, the 4096-grid batch, the adjoint at 2048^2) are reported under
+"forms" when requested with --forms.
+
+Arms:
+  default            the CUDA library (libcpb.so) through its C ABI.
+  --impl reference   the CPU oracle (the paper's execution model: tiled kernel
+                     run block by block with loop fission on a thread pool),
+                     timed on this machine's host cores on a bounded sample.
+
+Multi-GPU: one process per GPU (torchrun); every rank runs its own replica of
+the workload (the problems are independent, no collective on the data path);
+value = all ranks' cell updates / max-over-ranks time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Gcell-updates/s and % of HBM roofline (FP32 plain vs BF16/batched/adjoint)"
+UNIT = "Gcell-updates/s"
+BYTES_PER_CELL_PASS = {"f32": 16, "bf16k": 12}  # read u, kappa, s + write u, once per pass
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(times_ms, updates_per_rank):
+    """Whole-job throughput from per-rank times: all ranks' updates / max time."""
+    tmax = max(times_ms)
+    return sum(updates_per_rank) / (tmax * 1e-3) / 1e9, tmax
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        hi = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * hi] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(g, target_s=12.0):
+    """Time the fission oracle (FP32, all host cores) on the full grid for as
+    many time steps as fit in about target_s seconds.  Returns (Gcell/s, dict)."""
+    import oracle
+    cores = oracle.host_cores()
+    t0 = time.perf_counter()
+    oracle.fission(g.u, g.kappa, g.src, 1, g.dt, g.bc, "f32", block=(16, 16), pool=cores)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(target_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.fission(g.u, g.kappa, g.src, steps, g.dt, g.bc, "f32", block=(16, 16), pool=cores)
+    dt = time.perf_counter() - t0
+    rate = g.nx * g.ny * steps / dt / 1e9
+    return rate, {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                  "sample": f"{steps} time steps of the full {g.nx}x{g.ny} grid, tiled kernel "
+                            f"executed with loop fission on a {cores}-thread pool, FP32, "
+                            f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    g = W.plain_scale(seed=1, n=args.n, steps=args.time_steps)
+    cores = oracle.host_cores()
+    # Each bench step: a bounded sample of the workload (a few time steps of the
+    # full grid) sized so the whole run stays within a few minutes.
+    t0 = time.perf_counter()
+    oracle.fission(g.u, g.kappa, g.src, 1, g.dt, g.bc, "f32", pool=cores)
+    one = time.perf_counter() - t0
+    per_step = max(1, int(min(20.0, 150.0 / max(1, args.steps + args.warmup)) / max(one, 1e-3)))
+    for _ in range(args.warmup):
+        oracle.fission(g.u, g.kappa, g.src, per_step, g.dt, g.bc, "f32", pool=cores)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fission(g.u, g.kappa, g.src, per_step, g.dt, g.bc, "f32", pool=cores)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = g.nx * g.ny * per_step * args.steps / total / 1e9
+    sample = (f"{per_step} time steps of the full {g.nx}x{g.ny} grid per bench step, tiled kernel "
+              f"executed with loop fission on a {cores}-thread pool, FP32")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": g.name, "nx": g.nx, "ny": g.ny, "bc": "periodic",
+                       "time_steps_per_bench_step": per_step, "parallelism": "cpu thread pool"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2206_07896_gb300 as cpb
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device for the GPU arm")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    L = cpb.lib(fma=True)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    g = W.plain_scale(seed=1 + rank, n=args.n, steps=args.time_steps)
+    nx, ny, T = g.nx, g.ny, g.steps
+    u0 = torch.from_numpy(g.u).to(dev)
+    kap = torch.from_numpy(g.kappa).to(dev)
+    src = torch.from_numpy(g.src).to(dev)
+    a, b = torch.empty_like(u0), torch.empty_like(u0)
+
+    if args.k:
+        tuning = {"k": args.k, "chunk_rows": args.chunk, "warps_per_block": args.wpb, "variant": 0}
+    else:
+        a.copy_(u0)
+        tuning = L.cpb_autotune(a, b, kap, src, nx, ny, 24, float(g.dt), g.bc, cpb.CPB_F32, stream=sh)
+    k = tuning["k"]
+    depths = [k] * (T // k) + ([T % k] if T % k else [])
+    ws_bytes = L.cpb_heat_sum_workspace_bytes(nx, ny)
+    ws = torch.empty(max(8, ws_bytes) // 8, dtype=torch.float64, device=dev)
+    hsum = torch.empty((), dtype=torch.float64, device=dev)
+    n_pass = len(depths)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_pass + 1)]
+           for _ in range(args.steps)]
+
+    def one_step(ev=None):
+        # One bench step: T time steps in passes of depth k (ping-pong a/b,
+        # each pass one launch of the streaming kernel), then the FP64 heat sum
+        # of the result.  ev: CUDA events recorded around every pass.
+        src_buf, dst = u0, a
+        for i, d in enumerate(depths):
+            if ev is not None:
+                ev[i].record(stream)
+            L.cpb_stencil_launch_tuned(src_buf, dst, kap, src, nx, ny, d, float(g.dt), g.bc,
+                                       cpb.CPB_F32, tuning=tuning, scratch=None, stream=sh)
+            src_buf, dst = dst, (b if dst is a else a)
+        if ev is not None:
+            ev[n_pass].record(stream)
+        L.cpb_heat_sum(src_buf, nx, ny, cpb.CPB_F32, hsum, ws, ws_bytes, stream=sh)
+        return src_buf
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    full_pass_ms = []
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for st in range(args.steps):
+            one_step(evs[st])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    # per-launch durations of the dominant kernel (the full-depth passes)
+    for ev in evs:
+        for i, d in enumerate(depths):
+            if d == k:
+                full_pass_ms.append(ev[i].elapsed_time(ev[i + 1]))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    elapsed = start.elapsed_time(stop)
+    per_rank_ms = elapsed / args.steps
+    updates = nx * ny * T
+    if pg:
+        t = torch.tensor([per_rank_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tmax = float(t.item())
+    else:
+        tmax = per_rank_ms
+    value = updates * world / (tmax * 1e-3) / 1e9
+
+    # Roofline of the dominant kernel (full-depth stream pass).
+    hbm, which = peaks()
+    avg_pass = sum(full_pass_ms) / len(full_pass_ms)
+    alg_bytes = BYTES_PER_CELL_PASS["f32"] * nx * ny
+    achieved = alg_bytes / (avg_pass * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": args.traffic, "peak_source": which,
+            "kernel": f"stream_kernel<K={k},f32>", "avg_launch_ms": avg_pass,
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "effective_cell_rate_vs_k1_roofline": value / world / (hbm * 1e9 / 16 / 1e9)}
+
+    # End to end through the C ABI on host buffers (pinned), copies timed.
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.from_numpy(g.u).pin_memory()
+        hk = torch.from_numpy(g.kappa).pin_memory()
+        hs = torch.from_numpy(g.src).pin_memory()
+        ho = torch.empty_like(hu).pin_memory()
+        L.cpb_set_tuning(nx, ny, cpb.CPB_F32, g.bc, tuning)
+        wsb = L.cpb_host_workspace_bytes(nx, ny, cpb.CPB_F32)
+        hws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        L.cpb_stencil_host(hu, hk, hs, ho, nx, ny, T, float(g.dt), g.bc, cpb.CPB_F32, hws, wsb,
+                           stream=sh)
+        reps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            L.cpb_stencil_host(hu, hk, hs, ho, nx, ny, T, float(g.dt), g.bc, cpb.CPB_F32, hws, wsb,
+                               stream=sh)
+        e2e_s = (time.perf_counter() - t0) / reps
+        if pg:
+            t = torch.tensor([e2e_s], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": updates * world / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * nx * ny * 4, "d2h_bytes_per_step": nx * ny * 4,
+               "ms_per_step": e2e_s * 1e3}
+        del hws
+
+    forms = None
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            _, cpu = oracle_sample(g)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": g.name, "nx": nx, "ny": ny, "time_steps": T,
+                           "bc": "periodic", "tuning": tuning,
+                           "l2": "inputs larger than L2 (u, kappa, s, 2 ping-pong buffers: 256 MiB each)",
+                           "parallelism": f"replicas x{world}",
+                           "step": "1000 time steps + FP64 heat sum"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * (n_pass + 2), "clocks": clocks.summary()}
+        if forms is not None:
+            line["forms"] = forms
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192, help="grid side (default 8192)")
+    ap.add_argument("--time-steps", type=int, default=1000)
+    ap.add_argument("--k", type=int, default=0, help="force temporal depth (0 = autotune)")
+    ap.add_argument("--chunk", type=int, default=256)
+    ap.add_argument("--wpb", type=int, default=4)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the dominant kernel, if measured")
+    ap.add_argument("--forms", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
