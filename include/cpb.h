@@ -78,13 +78,21 @@ typedef struct {
 /* Parameters of the streaming temporal-blocked kernel (the tuned path).
  *   k               time steps fused per pass over HBM (temporal block depth), 1..8
  *   chunk_rows      output rows per warp work item (>= 1)
- *   warps_per_block warps per CTA (1..32)
- *   variant         0 = register-streaming with 128-bit loads (only variant) */
+ *   warps_per_block warps per CTA (1..8)
+ *   variant         0 = each lane loads its 128-bit slice of the next row into
+ *                       registers (any size, any alignment);
+ *                   1 = per-warp ring of shared-memory row slots filled by TMA
+ *                       bulk copies (cp.async.bulk + mbarrier).  Used when the
+ *                       fields are 16-byte aligned, nx % 4 == 0 and nx >= 128
+ *                       (BF16-Kahan: nx % 8 == 0, nx >= 136); otherwise
+ *                       variant 0 runs with the same results.
+ *   stages          variant 1: ring slots per warp, a power of two in 2..16 */
 typedef struct {
   int k;
   int chunk_rows;
   int warps_per_block;
   int variant;
+  int stages;
 } cpb_tuning;
 
 int cpb_version(void);
@@ -133,6 +141,16 @@ cpb_status cpb_get_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_
 cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src, int nx, int ny,
                         int steps, float dt, cpb_boundary bc, cpb_dtype dtype, cpb_stream_t stream,
                         cpb_tuning* best);
+
+/* Device status word of the stream kernels: synchronises the device, returns
+ * in *status CPB_SUCCESS or CPB_ERR_TIMEOUT (a bounded mbarrier wait in a
+ * variant-1 kernel gave up; that kernel's output is invalid), and clears it. */
+cpb_status cpb_device_status(int* status);
+
+/* Test hook: mbarrier wait limit in polls (<= 0: default, about 4M polls) and
+ * a row index whose copies are made to never complete (-1: off), applied to
+ * subsequent launches of this process.  Used to exercise the timeout path. */
+cpb_status cpb_debug_set(int wait_limit, int inject_row);
 
 /* FP64 sum of the field (CPB_F32: sum of (double)u; CPB_BF16_KAHAN: sum of
  * (double)hi - (double)cmp), written to *d_out (device pointer).  Two

@@ -48,7 +48,7 @@ class cpb_dim3(C.Structure):
 
 class cpb_tuning(C.Structure):
     _fields_ = [("k", C.c_int), ("chunk_rows", C.c_int), ("warps_per_block", C.c_int),
-                ("variant", C.c_int)]
+                ("variant", C.c_int), ("stages", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -69,6 +69,8 @@ _SIGS = {
     "cpb_set_tuning": (_i, [_i, _i, _i, _i, C.POINTER(cpb_tuning)]),
     "cpb_get_tuning": (_i, [_i, _i, _i, _i, C.POINTER(cpb_tuning)]),
     "cpb_autotune": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, C.POINTER(cpb_tuning)]),
+    "cpb_device_status": (_i, [C.POINTER(_i)]),
+    "cpb_debug_set": (_i, [_i, _i]),
     "cpb_heat_sum_workspace_bytes": (_sz, [_i, _i]),
     "cpb_heat_sum": (_i, [_vp, _i, _i, _i, _vp, _vp, _sz, _vp]),
     "cpb_bf16_round": (_i, [_vp, _vp, _ll, _vp]),
@@ -182,6 +184,14 @@ class Library:
                    bc, dtype, stream_handle(stream), C.byref(t))
         return t.as_dict()
 
+    def cpb_device_status(self) -> int:
+        st = _i()
+        self._call("cpb_device_status", C.byref(st))
+        return st.value
+
+    def cpb_debug_set(self, wait_limit, inject_row):
+        self._call("cpb_debug_set", wait_limit, inject_row)
+
     def cpb_heat_sum_workspace_bytes(self, nx, ny) -> int:
         return self._lib.cpb_heat_sum_workspace_bytes(nx, ny)
 
@@ -227,7 +237,7 @@ def as_tuning(t) -> cpb_tuning:
         return t
     if isinstance(t, dict):
         return cpb_tuning(int(t["k"]), int(t["chunk_rows"]), int(t.get("warps_per_block", 4)),
-                          int(t.get("variant", 0)))
+                          int(t.get("variant", 0)), int(t.get("stages", 8)))
     return cpb_tuning(*[int(v) for v in t])
 
 

@@ -63,24 +63,43 @@ using TuneKey = std::tuple<int, int, int, int>;
 std::mutex g_tune_mutex;
 std::map<TuneKey, cpb_tuning> g_tune;
 
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
 bool tuning_valid(const cpb_tuning& t) {
-  return t.k >= 1 && t.k <= 8 && t.chunk_rows >= 1 && t.warps_per_block >= 1 &&
-         t.warps_per_block <= 8 && t.variant == 0;
+  if (t.k < 1 || t.k > 8 || t.chunk_rows < 1 || t.warps_per_block < 1 || t.warps_per_block > 8)
+    return false;
+  if (t.variant == 0) return true;
+  return t.variant == 1 && pow2(t.stages) && t.stages >= 2 && t.stages <= 16 &&
+         bulk_smem_bytes(false, t.warps_per_block, t.stages) <= 227 * 1024;
 }
 
-// Built-in default: depth 4, and chunks sized so the grid yields about 16
-// warp items per SM (one resident wave at the kernel's register footprint).
+// Variant 1 (TMA bulk-copy ring) needs aligned rows; otherwise variant 0 runs.
+bool bulk_eligible(int nx, cpb_dtype d, bool vec, const void* kappa, const void* src) {
+  const bool bf = d == CPB_BF16_KAHAN;
+  return vec && nx % bulk_align_cells(bf) == 0 && nx >= bulk_slot_cells(bf) && aligned(kappa, 16) &&
+         aligned(src, 16);
+}
+
+// Built-in default (the autotuner's usual winner on GB300 at large sizes):
+// TMA ring of 8 stages, depth 6, and chunks sized so the grid yields about
+// one resident wave of warp items.
 cpb_tuning default_tuning(int nx, int ny, cpb_dtype) {
   cpb_tuning t;
-  t.k = 4;
+  t.k = 6;
   t.warps_per_block = 4;
-  t.variant = 0;
+  t.variant = 1;
+  t.stages = 8;
   const long long strips = (nx + strip_out_width(t.k) - 1) / strip_out_width(t.k);
-  const long long target = (long long)device_sm_count() * 12;
+  const long long target = (long long)device_sm_count() * 8;
   long long rows = (strips * ny + target - 1) / target;
   t.chunk_rows = (int)std::max(16LL, std::min(rows, 1024LL));
   return t;
 }
+
+// Debug knobs (tests only): mbarrier wait limit and an injected row whose
+// copies never complete.
+int g_wait_limit = 1 << 22;
+int g_inject_row = -1;
 
 cpb_tuning lookup_tuning(int nx, int ny, cpb_dtype d, cpb_boundary bc) {
   std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -171,6 +190,10 @@ cpb_status enqueue_tuned(const Fields& f, int nx, int ny, int steps, float dt, c
           aligned(f.kappa, ka) && aligned(f.src, ka);
   p.chunk_rows = t.chunk_rows;
   p.warps_per_block = t.warps_per_block;
+  p.variant = (t.variant == 1 && bulk_eligible(nx, dtype, p.vec != 0, f.kappa, f.src)) ? 1 : 0;
+  p.stages = t.stages;
+  p.wait_limit = g_wait_limit;
+  p.inject_row = g_inject_row;
 
   bool copy_at_end = false;
   std::vector<int> depths = pass_depths(steps, t.k, f.scratch != nullptr, &copy_at_end);
@@ -186,8 +209,8 @@ cpb_status enqueue_tuned(const Fields& f, int nx, int ny, int steps, float dt, c
       dst = (i % 2 == 0) ? f.u_out : f.u_in;
     p.u_in = src_buf;
     p.u_out = dst;
-    cudaError_t e = dtype == CPB_F32 ? launch_stream_f32(p, depths[i], s)
-                                     : launch_stream_bf16k(p, depths[i], s);
+    p.depth = depths[i];
+    cudaError_t e = dtype == CPB_F32 ? launch_stream_f32(p, t.k, s) : launch_stream_bf16k(p, t.k, s);
     CPB_TRY(e);
     src_buf = dst;
   }
@@ -317,8 +340,10 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
   if (st != CPB_SUCCESS) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int ks[] = {1, 2, 3, 4, 5, 6, 8};
-  const int chunks[] = {32, 64, 128, 256, 512};
-  const int wpbs[] = {2, 4, 8};
+  const int chunks[] = {64, 128, 256, 512};
+  const int wpbs[] = {2, 4};
+  const int variants[] = {0, 1};
+  const int stages_list[] = {4, 8};
   cudaEvent_t e0, e1;
   CPB_TRY(cudaEventCreate(&e0));
   CPB_TRY(cudaEventCreate(&e1));
@@ -327,9 +352,13 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
   const int probe = steps >= 1 ? steps : 16;
   for (int k : ks)
     for (int c : chunks)
-      for (int w : wpbs) {
+      for (int w : wpbs)
+        for (int v : variants)
+          for (int st : stages_list) {
         if (c > 2 * ny && c != chunks[0]) continue;
-        cpb_tuning t{k, c, w, 0};
+        if (v == 0 && st != stages_list[0]) continue;
+        cpb_tuning t{k, c, w, v, st};
+        if (!tuning_valid(t)) continue;
         // Probe length: a multiple of k near `probe` so every pass has depth k.
         int n = std::max(k, (probe / k) * k);
         cpb_status r = enqueue_tuned(f, nx, ny, n, dt, bc, dtype, t, s);  // warm-up
@@ -351,6 +380,22 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
   CPB_TRY(cudaGetLastError());
   cpb_set_tuning(nx, ny, dtype, bc, &bt);
   if (best) *best = bt;
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_device_status(int* status) {
+  if (!status) return CPB_ERR_INVALID_VALUE;
+  CPB_TRY(cudaDeviceSynchronize());
+  int a = 0, b = 0;
+  CPB_TRY(read_stream_status_f32(&a));
+  CPB_TRY(read_stream_status_bf16k(&b));
+  *status = a ? a : b;
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_debug_set(int wait_limit, int inject_row) {
+  g_wait_limit = wait_limit > 0 ? wait_limit : (1 << 22);
+  g_inject_row = inject_row;
   return CPB_SUCCESS;
 }
 

@@ -19,15 +19,32 @@ struct StreamPass {
   int vec;          // 1: 128-bit access path (nx % 4 == 0, aligned pointers)
   int chunk_rows;   // output rows per warp item
   int warps_per_block;
+  int depth;        // time steps of this pass (<= the instantiated depth K)
+  int variant;      // 0: register prefetch, 1: TMA bulk-copy ring
+  int stages;       // variant 1: ring slots per warp (power of two, 2..16)
+  int wait_limit;   // variant 1: mbarrier polls before a wait gives up
+  int inject_row;   // variant 1, tests only: a row whose copies never complete (-1: off)
 };
 
 // Number of output columns per warp strip for temporal depth k (128 columns
 // per warp minus a halo of k rounded up to a multiple of 4 on each side).
 inline int strip_out_width(int k) { return 128 - 2 * ((k + 3) & ~3); }
 
-// One pass of depth k (1..8) over the whole grid.  Returns the launch error.
+// Variant 1 ring geometry: cells per slot row and the column alignment
+// (in cells) that keeps every bulk copy on 16-byte boundaries.
+inline int bulk_slot_cells(bool bf16) { return bf16 ? 136 : 128; }
+inline int bulk_align_cells(bool bf16) { return bf16 ? 8 : 4; }
+inline size_t bulk_smem_bytes(bool bf16, int warps, int stages) {
+  const size_t slot = (size_t)bulk_slot_cells(bf16) * (bf16 ? 4 + 2 + 2 : 4 + 4 + 4);
+  return (size_t)warps * stages * (slot + sizeof(uint64_t));
+}
+
+// One pass of instantiated depth k (1..8) over the whole grid.
 cudaError_t launch_stream_f32(const StreamPass& p, int k, cudaStream_t s);
 cudaError_t launch_stream_bf16k(const StreamPass& p, int k, cudaStream_t s);
+// Read and clear the device status word of the f32 / bf16 stream kernels.
+cudaError_t read_stream_status_f32(int* out);
+cudaError_t read_stream_status_bf16k(int* out);
 
 // The tiled one-step kernel (bx x by threads, one cell each).
 cudaError_t launch_tile_f32(const float* u_in, float* u_out, const float* kappa, const float* src,

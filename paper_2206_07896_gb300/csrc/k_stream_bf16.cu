@@ -1,8 +1,9 @@
-// BF16-Kahan-storage instantiations of the streaming temporal-blocked kernel.
+// BF16-Kahan-storage instantiations of the streaming temporal-blocked kernels.
 #include "k_stream.cuh"
 
 namespace cpb {
 cudaError_t launch_stream_bf16k(const StreamPass& p, int k, cudaStream_t s) {
   return launch_stream_any<true>(p, k, s);
 }
+cudaError_t read_stream_status_bf16k(int* out) { return read_stream_status(out); }
 }  // namespace cpb

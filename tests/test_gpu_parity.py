@@ -306,7 +306,8 @@ def test_tuning_cache_and_autotune(dev, exact):
     u, k, s = to_dev(g.u, dev), to_dev(g.kappa, dev), to_dev(g.src, dev)
     exact.cpb_set_tuning(640, 256, cpb.CPB_F32, P, {"k": 3, "chunk_rows": 40, "warps_per_block": 2})
     assert exact.cpb_get_tuning(640, 256, cpb.CPB_F32, P) == {"k": 3, "chunk_rows": 40,
-                                                             "warps_per_block": 2, "variant": 0}
+                                                             "warps_per_block": 2, "variant": 0,
+                                                             "stages": 8}
     best = exact.cpb_autotune(u.clone(), torch.empty_like(u), k, s, 640, 256, 8, float(g.dt), P,
                               cpb.CPB_F32)
     assert exact.cpb_get_tuning(640, 256, cpb.CPB_F32, P) == best
@@ -332,3 +333,52 @@ def test_host_end_to_end(dev, exact, dtype):
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     exact.cpb_stencil_host(u0, kk, ss, out, g.nx, g.ny, g.steps, float(g.dt), D, dtype, ws, wsb)
     np.testing.assert_array_equal(out, ref)
+
+
+# ---------------------------------------------------------------------------
+# variant 1: TMA bulk-copy ring
+# ---------------------------------------------------------------------------
+BULK_SHAPES = [(256, 130), (272, 97), (1024, 33), (128, 300), (144, 8)]
+
+
+@pytest.mark.parametrize("bc", [D, P])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_bulk_variant_bit_exact(dev, exact, bc, k):
+    for (nx, ny) in BULK_SHAPES:
+        for steps in (1, 2 * k + 1):
+            g = W.random_grid(nx * 3 + ny + k, nx, ny, steps, bc)
+            ref = oracle.direct(g.u, g.kappa, g.src, steps, g.dt, bc, "f32")
+            for chunk, wpb, stages in ((16, 4, 8), (7, 1, 2), (64, 8, 4), (300, 2, 16)):
+                t = {"k": k, "chunk_rows": chunk, "warps_per_block": wpb, "variant": 1,
+                     "stages": stages}
+                for scratch in (True, False):
+                    got = run_tuned(exact, g, dev, t, scratch=scratch)
+                    np.testing.assert_array_equal(got, ref, err_msg=f"{nx}x{ny} steps={steps} {t}")
+    assert exact.cpb_device_status() == 0
+
+
+@pytest.mark.parametrize("bc", [D, P])
+@pytest.mark.parametrize("k", [1, 4, 6, 8])
+def test_bulk_variant_bf16k_bit_exact(dev, exact, bc, k):
+    for (nx, ny) in [(272, 70), (136, 50), (400, 9)]:
+        g = W.random_grid(nx + ny + k, nx, ny, 2 * k + 1, bc)
+        st = oracle.bf16k_pack(g.u)
+        kb, sb = oracle.bf16_round(g.kappa), oracle.bf16_round(g.src)
+        ref = oracle.direct_bf16k(st, kb, sb, g.steps, g.dt, bc)
+        fields = (to_dev(st.view(np.int32), dev), to_dev(kb.view(np.int16), dev),
+                  to_dev(sb.view(np.int16), dev))
+        for stages in (2, 8):
+            got = run_tuned(exact, g, dev, {"k": k, "chunk_rows": 24, "warps_per_block": 2,
+                                            "variant": 1, "stages": stages},
+                            dtype=cpb.CPB_BF16_KAHAN, fields=fields)
+            np.testing.assert_array_equal(got.view(np.uint32), ref)
+    assert exact.cpb_device_status() == 0
+
+
+def test_bulk_variant_fma_build_within_tolerance(dev, fast):
+    g = W.random_grid(21, 1024, 512, 1000, P, r=0.24)
+    ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, P, "f64", pool=8)
+    got = run_tuned(fast, g, dev, {"k": 6, "chunk_rows": 128, "warps_per_block": 4, "variant": 1,
+                                   "stages": 8})
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= 1e-5, err
