@@ -147,7 +147,7 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
  * variant-1 kernel gave up; that kernel's output is invalid), and clears it. */
 cpb_status cpb_device_status(int* status);
 
-/* Test hook: mbarrier wait limit in polls (<= 0: default, about 4M polls) and
+/* Test hook: mbarrier wait limit in polls (<= 0: default, about 1M polls) and
  * a row index whose copies are made to never complete (-1: off), applied to
  * subsequent launches of this process.  Used to exercise the timeout path. */
 cpb_status cpb_debug_set(int wait_limit, int inject_row);
@@ -178,6 +178,81 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
                             void* u_out_host, int nx, int ny, int steps, float dt, cpb_boundary bc,
                             cpb_dtype dtype, void* d_workspace, size_t ws_bytes,
                             cpb_stream_t stream);
+
+/* Batched persistent stencil: many independent grids (uneven sizes and step
+ * counts, CPB_F32 storage, one boundary rule) advanced in ONE kernel launch.
+ * Resident CTAs fetch grids from a device work queue, `grain` grids per atomic
+ * fetch (the GPU counterpart of the paper's task queue with block_per_fetch,
+ * Sec. IV "Fetch task queue" and "Runtime Optimizations").  Grids with at
+ * least team_cells cells run on a whole CTA, smaller ones on one warp.
+ * Each grid's result is written to its u_out; its u_in is clobbered (used as
+ * the ping-pong buffer).  Every grid advances at temporal depth 4.
+ *
+ * cpb_batch_order (host): validates the host copy of the descriptors and
+ * writes the queue order into h_order[ngrids]: large grids first, each class
+ * longest-first (LPT by cells x steps), and *n_large.  Invalid descriptor ->
+ * CPB_ERR_INVALID_VALUE.
+ * cpb_stencil_batched: d_descs / d_order are device copies; d_work is device
+ * memory of cpb_batch_work_bytes() bytes (queue counters + status word), reset
+ * by the call itself (the call is one memset + one kernel launch, so it can be
+ * captured in a CUDA graph).  plan == NULL or plan->blocks <= 0 fills the GPU.
+ * cpb_batch_status: synchronises `stream` and returns the status word
+ * (CPB_SUCCESS, or CPB_ERR_INVALID_VALUE if a device descriptor was invalid). */
+typedef struct {
+  void* u_in;
+  void* u_out;
+  const void* kappa;
+  const void* src; /* may be NULL: no source */
+  int nx, ny, steps;
+  float dt;
+} cpb_grid_desc;
+
+typedef struct {
+  int grain;      /* grids per queue fetch (>= 1) */
+  int blocks;     /* persistent CTAs (<= 0: one wave filling the GPU) */
+  int threads;    /* threads per CTA, a multiple of 32, <= 384 */
+  int team_cells; /* grids with nx*ny >= team_cells run on a whole CTA */
+} cpb_batch_plan;
+
+cpb_status cpb_batch_plan_default(cpb_batch_plan* plan);
+cpb_status cpb_batch_order(const cpb_grid_desc* h_descs, int ngrids, const cpb_batch_plan* plan,
+                           int* h_order, int* n_large);
+size_t cpb_batch_work_bytes(void);
+cpb_status cpb_stencil_batched(const cpb_grid_desc* d_descs, const int* d_order, int ngrids,
+                               int n_large, cpb_dtype dtype, cpb_boundary bc,
+                               const cpb_batch_plan* plan, int* d_work, cpb_stream_t stream);
+cpb_status cpb_batch_status(const int* d_work, int* status, cpb_stream_t stream);
+
+/* Discrete adjoint of the N-step stencil (CPB_F32), for gradients of a loss
+ * L(u_T) with respect to u_0 and kappa.  With lambda_T = dL/du_T (given):
+ *   lambda_n = lambda_{n+1} + dt D(kappa) lambda_{n+1}   (D symmetric: the
+ *              same update with s = 0), dL/du_0 = lambda_0,
+ *   dL/dkappa_c = sum over steps and faces f of c, with u = u_n and
+ *              lambda = lambda_{n+1}: hdt (u_f - u_c)(lambda_c - lambda_f) for
+ *              an interior face, dt (0 - u_c) lambda_c for a Dirichlet
+ *              boundary face.
+ * The paper has no adjoint; this is the derivative of the update defined
+ * above.  States are checkpointed every ckpt_every steps by the forward call
+ * and each segment is recomputed during the backward sweep.
+ *
+ * workspace: device memory of cpb_adjoint_workspace_bytes() bytes, 256-byte
+ * aligned, holding the checkpoints between cpb_adjoint_forward and
+ * cpb_adjoint_backward (same nx, ny, steps, dt, bc, ckpt_every, kappa, src).
+ * cpb_adjoint_forward writes u_T.  cpb_adjoint_backward overwrites grad_u0
+ * and grad_kappa.  cpb_stencil_adjoint runs both (u_T is not returned).
+ * src may be NULL (no source).  All asynchronous on `stream`. */
+size_t cpb_adjoint_workspace_bytes(int nx, int ny, int steps, int ckpt_every);
+cpb_status cpb_adjoint_forward(const float* u0, const float* kappa, const float* src, int nx, int ny,
+                               int steps, float dt, cpb_boundary bc, int ckpt_every, float* u_T,
+                               void* workspace, size_t ws_bytes, cpb_stream_t stream);
+cpb_status cpb_adjoint_backward(const float* kappa, const float* src, const float* lambda_T, int nx,
+                                int ny, int steps, float dt, cpb_boundary bc, int ckpt_every,
+                                float* grad_u0, float* grad_kappa, void* workspace, size_t ws_bytes,
+                                cpb_stream_t stream);
+cpb_status cpb_stencil_adjoint(const float* u0, const float* kappa, const float* src,
+                               const float* lambda_T, int nx, int ny, int steps, float dt,
+                               cpb_boundary bc, int ckpt_every, float* grad_u0, float* grad_kappa,
+                               void* workspace, size_t ws_bytes, cpb_stream_t stream);
 
 /* CUDA graph of a whole multi-step run (the launch sequence captured once and
  * replayed; Sec. VI of the paper measures launch + sync overhead of many

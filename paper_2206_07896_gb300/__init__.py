@@ -46,6 +46,20 @@ class cpb_dim3(C.Structure):
     _fields_ = [("x", C.c_uint), ("y", C.c_uint), ("z", C.c_uint)]
 
 
+class cpb_grid_desc(C.Structure):
+    _fields_ = [("u_in", C.c_void_p), ("u_out", C.c_void_p), ("kappa", C.c_void_p),
+                ("src", C.c_void_p), ("nx", C.c_int), ("ny", C.c_int), ("steps", C.c_int),
+                ("dt", C.c_float)]
+
+
+class cpb_batch_plan(C.Structure):
+    _fields_ = [("grain", C.c_int), ("blocks", C.c_int), ("threads", C.c_int),
+                ("team_cells", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class cpb_tuning(C.Structure):
     _fields_ = [("k", C.c_int), ("chunk_rows", C.c_int), ("warps_per_block", C.c_int),
                 ("variant", C.c_int), ("stages", C.c_int)]
@@ -78,6 +92,16 @@ _SIGS = {
     "cpb_bf16k_unpack": (_i, [_vp, _vp, _ll, _vp]),
     "cpb_host_workspace_bytes": (_sz, [_i, _i, _i]),
     "cpb_stencil_host": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _sz, _vp]),
+    "cpb_batch_plan_default": (_i, [C.POINTER(cpb_batch_plan)]),
+    "cpb_batch_order": (_i, [_vp, _i, C.POINTER(cpb_batch_plan), _vp, C.POINTER(_i)]),
+    "cpb_batch_work_bytes": (_sz, []),
+    "cpb_stencil_batched": (_i, [_vp, _vp, _i, _i, _i, _i, C.POINTER(cpb_batch_plan), _vp, _vp]),
+    "cpb_batch_status": (_i, [_vp, C.POINTER(_i), _vp]),
+    "cpb_adjoint_workspace_bytes": (_sz, [_i, _i, _i, _i]),
+    "cpb_adjoint_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _vp, _sz, _vp]),
+    "cpb_adjoint_backward": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _vp, _vp, _sz, _vp]),
+    "cpb_stencil_adjoint": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _vp, _vp, _sz,
+                                 _vp]),
     "cpb_graph_create": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, C.POINTER(cpb_tuning),
                               _vp, C.POINTER(_vp)]),
     "cpb_graph_launch": (_i, [_vp, _vp]),
@@ -217,6 +241,55 @@ class Library:
                    host_ptr(u_out_host), nx, ny, steps, float(dt), bc, dtype, ptr(d_workspace),
                    ws_bytes, stream_handle(stream))
 
+    def cpb_batch_plan_default(self) -> dict:
+        p = cpb_batch_plan()
+        self._call("cpb_batch_plan_default", C.byref(p))
+        return p.as_dict()
+
+    def cpb_batch_order(self, h_descs, plan=None):
+        """h_descs: ctypes array of cpb_grid_desc.  Returns (order list, n_large)."""
+        n = len(h_descs)
+        order = (C.c_int * max(n, 1))()
+        nl = _i()
+        pl = C.byref(as_plan(plan)) if plan is not None else None
+        self._call("cpb_batch_order", C.addressof(h_descs) if n else None, n, pl, C.addressof(order),
+                   C.byref(nl))
+        return list(order[:n]), nl.value
+
+    def cpb_batch_work_bytes(self) -> int:
+        return self._lib.cpb_batch_work_bytes()
+
+    def cpb_stencil_batched(self, d_descs, d_order, ngrids, n_large, dtype, bc, plan=None,
+                            d_work=None, stream=None):
+        pl = C.byref(as_plan(plan)) if plan is not None else None
+        self._call("cpb_stencil_batched", ptr(d_descs), ptr(d_order), ngrids, n_large, dtype, bc, pl,
+                   ptr(d_work), stream_handle(stream))
+
+    def cpb_batch_status(self, d_work, stream=None) -> int:
+        st = _i()
+        self._call("cpb_batch_status", ptr(d_work), C.byref(st), stream_handle(stream))
+        return st.value
+
+    def cpb_adjoint_workspace_bytes(self, nx, ny, steps, ckpt_every) -> int:
+        return self._lib.cpb_adjoint_workspace_bytes(nx, ny, steps, ckpt_every)
+
+    def cpb_adjoint_forward(self, u0, kappa, src, nx, ny, steps, dt, bc, ckpt_every, u_T, workspace,
+                            ws_bytes, stream=None):
+        self._call("cpb_adjoint_forward", ptr(u0), ptr(kappa), ptr(src), nx, ny, steps, float(dt), bc,
+                   ckpt_every, ptr(u_T), ptr(workspace), ws_bytes, stream_handle(stream))
+
+    def cpb_adjoint_backward(self, kappa, src, lambda_T, nx, ny, steps, dt, bc, ckpt_every, grad_u0,
+                             grad_kappa, workspace, ws_bytes, stream=None):
+        self._call("cpb_adjoint_backward", ptr(kappa), ptr(src), ptr(lambda_T), nx, ny, steps,
+                   float(dt), bc, ckpt_every, ptr(grad_u0), ptr(grad_kappa), ptr(workspace), ws_bytes,
+                   stream_handle(stream))
+
+    def cpb_stencil_adjoint(self, u0, kappa, src, lambda_T, nx, ny, steps, dt, bc, ckpt_every,
+                            grad_u0, grad_kappa, workspace, ws_bytes, stream=None):
+        self._call("cpb_stencil_adjoint", ptr(u0), ptr(kappa), ptr(src), ptr(lambda_T), nx, ny, steps,
+                   float(dt), bc, ckpt_every, ptr(grad_u0), ptr(grad_kappa), ptr(workspace), ws_bytes,
+                   stream_handle(stream))
+
     def cpb_graph_create(self, u_in, u_out, kappa, src, nx, ny, steps, dt, bc, dtype, tuning=None,
                          scratch=None) -> int:
         g = _vp()
@@ -239,6 +312,14 @@ def as_tuning(t) -> cpb_tuning:
         return cpb_tuning(int(t["k"]), int(t["chunk_rows"]), int(t.get("warps_per_block", 4)),
                           int(t.get("variant", 0)), int(t.get("stages", 8)))
     return cpb_tuning(*[int(v) for v in t])
+
+
+def as_plan(p) -> cpb_batch_plan:
+    if isinstance(p, cpb_batch_plan):
+        return p
+    d = {"grain": 1, "blocks": 0, "threads": 384, "team_cells": 65536}
+    d.update(p)
+    return cpb_batch_plan(int(d["grain"]), int(d["blocks"]), int(d["threads"]), int(d["team_cells"]))
 
 
 _LIBS: dict[bool, Library] = {}
@@ -288,3 +369,72 @@ def heat_sum(u, dtype=CPB_F32, library: Library | None = None, stream=None):
     out = torch.empty((), dtype=torch.float64, device=u.device)
     L.cpb_heat_sum(u, nx, ny, dtype, out, ws, ws_bytes, stream=stream)
     return out
+
+
+def batch_descriptors(u_in, u_out, kappa, src, offsets, nx, ny, steps, dt):
+    """Descriptors of grids packed back to back in flat device tensors.
+
+    u_in/u_out/kappa/src: flat float32 CUDA tensors holding every grid (src may
+    be None); offsets/nx/ny/steps/dt: per-grid sequences (element offsets).
+    Returns a ctypes array of cpb_grid_desc (host memory)."""
+    n = len(nx)
+    arr = (cpb_grid_desc * n)()
+    bu, bo, bk = ptr(u_in), ptr(u_out), ptr(kappa)
+    bs = ptr(src) if src is not None else None
+    for g in range(n):
+        off = 4 * int(offsets[g])
+        arr[g] = cpb_grid_desc(bu + off, bo + off, bk + off, (bs + off) if bs is not None else None,
+                               int(nx[g]), int(ny[g]), int(steps[g]), float(dt[g]))
+    return arr
+
+
+def to_device_bytes(carray, device):
+    """Copy a ctypes array (descriptors or int order) into a CUDA uint8 tensor."""
+    import torch
+    raw = bytes(carray) if len(carray) else b"\0"
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
+def _stencil_fn():
+    import torch
+
+    class StencilFn(torch.autograd.Function):
+        """u_T = N steps of the stencil from u0; differentiable w.r.t. u0 and kappa.
+
+        apply(u0, kappa, src, steps, dt, bc=CPB_DIRICHLET0, ckpt_every=20, library=None)
+        Forward keeps checkpoints every `ckpt_every` steps in a workspace; backward
+        runs the library's adjoint (cpb_adjoint_backward).  FP32 storage."""
+
+        @staticmethod
+        def forward(ctx, u0, kappa, src, steps, dt, bc=CPB_DIRICHLET0, ckpt_every=20, library=None):
+            L = library or lib()
+            ny, nx = u0.shape
+            wsb = L.cpb_adjoint_workspace_bytes(nx, ny, steps, ckpt_every)
+            ws = torch.empty(wsb, dtype=torch.uint8, device=u0.device)
+            u0c, kc = u0.contiguous(), kappa.contiguous()
+            sc = src.contiguous() if src is not None else None
+            uT = torch.empty_like(u0c)
+            L.cpb_adjoint_forward(u0c, kc, sc, nx, ny, steps, dt, bc, ckpt_every, uT, ws, wsb)
+            ctx.save_for_backward(kc)
+            ctx.extra = (sc, ws, wsb, nx, ny, steps, dt, bc, ckpt_every, L)
+            return uT
+
+        @staticmethod
+        def backward(ctx, grad_uT):
+            (kc,) = ctx.saved_tensors
+            sc, ws, wsb, nx, ny, steps, dt, bc, ckpt_every, L = ctx.extra
+            g = grad_uT.contiguous()
+            gu0 = torch.empty_like(g)
+            gk = torch.empty_like(g)
+            L.cpb_adjoint_backward(kc, sc, g, nx, ny, steps, dt, bc, ckpt_every, gu0, gk, ws, wsb)
+            return gu0, gk, None, None, None, None, None, None
+
+    return StencilFn
+
+
+def __getattr__(name):
+    if name == "StencilFn":
+        fn = _stencil_fn()
+        globals()["StencilFn"] = fn
+        return fn
+    raise AttributeError(name)

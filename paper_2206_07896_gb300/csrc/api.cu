@@ -98,8 +98,9 @@ cpb_tuning default_tuning(int nx, int ny, cpb_dtype) {
 
 // Debug knobs (tests only): mbarrier wait limit and an injected row whose
 // copies never complete.
-int g_wait_limit = 1 << 22;
-int g_inject_row = -1;
+int g_wait_limit = 1 << 20;
+int g_inject_on = 0;
+int g_inject_row = 0;
 
 cpb_tuning lookup_tuning(int nx, int ny, cpb_dtype d, cpb_boundary bc) {
   std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -193,6 +194,7 @@ cpb_status enqueue_tuned(const Fields& f, int nx, int ny, int steps, float dt, c
   p.variant = (t.variant == 1 && bulk_eligible(nx, dtype, p.vec != 0, f.kappa, f.src)) ? 1 : 0;
   p.stages = t.stages;
   p.wait_limit = g_wait_limit;
+  p.inject_on = g_inject_on;
   p.inject_row = g_inject_row;
 
   bool copy_at_end = false;
@@ -394,7 +396,8 @@ cpb_status cpb_device_status(int* status) {
 }
 
 cpb_status cpb_debug_set(int wait_limit, int inject_row) {
-  g_wait_limit = wait_limit > 0 ? wait_limit : (1 << 22);
+  g_wait_limit = wait_limit > 0 ? wait_limit : (1 << 20);
+  g_inject_on = inject_row >= 0 ? 1 : 0;
   g_inject_row = inject_row;
   return CPB_SUCCESS;
 }
@@ -468,6 +471,206 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
   CPB_TRY(cudaMemcpyAsync(u_out_host, ubuf, ub, cudaMemcpyDeviceToHost, s));
   CPB_TRY(cudaStreamSynchronize(s));
   return CPB_SUCCESS;
+}
+
+cpb_status cpb_batch_plan_default(cpb_batch_plan* plan) {
+  if (!plan) return CPB_ERR_INVALID_VALUE;
+  plan->grain = 1;
+  plan->blocks = 0;
+  plan->threads = batch_threads_max();
+  plan->team_cells = 256 * 256;
+  return CPB_SUCCESS;
+}
+
+namespace {
+bool host_desc_ok(const cpb_grid_desc& g) {
+  return g.nx >= 1 && g.ny >= 1 && g.steps >= 0 && g.u_in && g.u_out && g.kappa &&
+         g.u_in != g.u_out && g.dt > 0.0f && std::isfinite(g.dt) &&
+         (long long)g.nx * g.ny <= (1LL << 31) && aligned(g.u_in, 4) && aligned(g.u_out, 4) &&
+         aligned(g.kappa, 4) && aligned(g.src, 4);
+}
+
+bool plan_ok(const cpb_batch_plan& p) {
+  return p.grain >= 1 && p.threads >= 32 && p.threads % 32 == 0 && p.threads <= batch_threads_max() &&
+         p.team_cells >= 1;
+}
+}  // namespace
+
+cpb_status cpb_batch_order(const cpb_grid_desc* h_descs, int ngrids, const cpb_batch_plan* plan,
+                           int* h_order, int* n_large) {
+  if (!h_descs || !h_order || !n_large || ngrids < 0) return CPB_ERR_INVALID_VALUE;
+  cpb_batch_plan p;
+  cpb_batch_plan_default(&p);
+  if (plan) p = *plan;
+  if (!plan_ok(p)) return CPB_ERR_INVALID_VALUE;
+  std::vector<int> large, small;
+  for (int i = 0; i < ngrids; ++i) {
+    if (!host_desc_ok(h_descs[i])) return CPB_ERR_INVALID_VALUE;
+    ((long long)h_descs[i].nx * h_descs[i].ny >= p.team_cells ? large : small).push_back(i);
+  }
+  auto cost = [&](int i) { return (double)h_descs[i].nx * h_descs[i].ny * (double)h_descs[i].steps; };
+  auto lpt = [&](int a, int b) { return cost(a) > cost(b) || (cost(a) == cost(b) && a < b); };
+  std::sort(large.begin(), large.end(), lpt);
+  std::sort(small.begin(), small.end(), lpt);
+  int o = 0;
+  for (int i : large) h_order[o++] = i;
+  for (int i : small) h_order[o++] = i;
+  *n_large = (int)large.size();
+  return CPB_SUCCESS;
+}
+
+size_t cpb_batch_work_bytes(void) { return 4 * sizeof(int); }
+
+cpb_status cpb_stencil_batched(const cpb_grid_desc* d_descs, const int* d_order, int ngrids,
+                               int n_large, cpb_dtype dtype, cpb_boundary bc,
+                               const cpb_batch_plan* plan, int* d_work, cpb_stream_t stream) {
+  if (ngrids < 0 || n_large < 0 || n_large > ngrids) return CPB_ERR_INVALID_VALUE;
+  if (bc != CPB_DIRICHLET0 && bc != CPB_PERIODIC) return CPB_ERR_INVALID_VALUE;
+  if (dtype != CPB_F32) return CPB_ERR_UNSUPPORTED_CONFIG;
+  if (!d_work || !aligned(d_work, 4)) return CPB_ERR_WORKSPACE;
+  if (ngrids > 0 && (!d_descs || !d_order)) return CPB_ERR_INVALID_VALUE;
+  cpb_batch_plan p;
+  cpb_batch_plan_default(&p);
+  if (plan) p = *plan;
+  if (!plan_ok(p)) return CPB_ERR_INVALID_VALUE;
+  int blocks = p.blocks;
+  if (blocks <= 0) {
+    int per_sm = 0;
+    CPB_TRY(batch_blocks_per_sm(p.threads, &per_sm));
+    blocks = std::max(1, per_sm) * device_sm_count();
+  }
+  return from_cuda(launch_batch(d_descs, d_order, ngrids, n_large, (int)bc, p.grain, blocks, p.threads,
+                                d_work, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+cpb_status cpb_batch_status(const int* d_work, int* status, cpb_stream_t stream) {
+  if (!d_work || !status) return CPB_ERR_INVALID_VALUE;
+  int w[4] = {0, 0, 0, 0};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CPB_TRY(cudaMemcpyAsync(w, d_work, sizeof(w), cudaMemcpyDeviceToHost, s));
+  CPB_TRY(cudaStreamSynchronize(s));
+  *status = w[2];
+  return CPB_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint with checkpointing
+// ---------------------------------------------------------------------------
+namespace {
+struct AdjointLayout {
+  size_t slot;  // bytes per field slot (256-aligned)
+  int nseg;     // checkpoints (states at m * ckpt)
+  int nsegbuf;  // recompute slots per segment (ckpt - 1)
+  size_t bytes;
+  float* ckpt(void* ws, int m) const { return reinterpret_cast<float*>(static_cast<char*>(ws) + m * slot); }
+  float* seg(void* ws, int q) const { return ckpt(ws, nseg + q); }
+  float* lam(void* ws, int i) const { return ckpt(ws, nseg + nsegbuf + i); }
+  float* tmp(void* ws) const { return ckpt(ws, nseg + nsegbuf + 2); }
+};
+
+AdjointLayout adjoint_layout(int nx, int ny, int steps, int ckpt) {
+  AdjointLayout L;
+  L.slot = align256((size_t)nx * ny * sizeof(float));
+  L.nseg = steps > 0 ? (steps + ckpt - 1) / ckpt : 0;
+  L.nsegbuf = std::max(0, std::min(ckpt, steps) - 1);
+  L.bytes = L.slot * (size_t)(std::max(L.nseg, 1) + L.nsegbuf + 3);
+  return L;
+}
+
+cpb_status adjoint_check(int nx, int ny, int steps, float dt, cpb_boundary bc, int ckpt, void* ws,
+                         size_t ws_bytes) {
+  if (nx < 1 || ny < 1 || steps < 0 || ckpt < 1) return CPB_ERR_INVALID_VALUE;
+  if (!(dt > 0.0f) || !std::isfinite(dt)) return CPB_ERR_INVALID_VALUE;
+  if (bc != CPB_DIRICHLET0 && bc != CPB_PERIODIC) return CPB_ERR_INVALID_VALUE;
+  if (!ws || !aligned(ws, 256) || ws_bytes < adjoint_layout(nx, ny, steps, ckpt).bytes)
+    return CPB_ERR_WORKSPACE;
+  return CPB_SUCCESS;
+}
+}  // namespace
+
+size_t cpb_adjoint_workspace_bytes(int nx, int ny, int steps, int ckpt_every) {
+  if (nx < 1 || ny < 1 || steps < 0 || ckpt_every < 1) return 0;
+  return adjoint_layout(nx, ny, steps, ckpt_every).bytes;
+}
+
+cpb_status cpb_adjoint_forward(const float* u0, const float* kappa, const float* src, int nx, int ny,
+                               int steps, float dt, cpb_boundary bc, int ckpt_every, float* u_T,
+                               void* workspace, size_t ws_bytes, cpb_stream_t stream) {
+  cpb_status st = adjoint_check(nx, ny, steps, dt, bc, ckpt_every, workspace, ws_bytes);
+  if (st != CPB_SUCCESS) return st;
+  if (!u0 || !kappa || !u_T || !aligned(u0, 4) || !aligned(kappa, 4) || !aligned(src, 4))
+    return CPB_ERR_INVALID_VALUE;
+  const AdjointLayout L = adjoint_layout(nx, ny, steps, ckpt_every);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t nb = (size_t)nx * ny * sizeof(float);
+  if (steps == 0) {
+    CPB_TRY(cudaMemcpyAsync(u_T, u0, nb, cudaMemcpyDeviceToDevice, s));
+    return CPB_SUCCESS;
+  }
+  const cpb_tuning t = lookup_tuning(nx, ny, CPB_F32, bc);
+  CPB_TRY(cudaMemcpyAsync(L.ckpt(workspace, 0), u0, nb, cudaMemcpyDeviceToDevice, s));
+  for (int m = 0; m < L.nseg; ++m) {
+    const int len = std::min(ckpt_every, steps - m * ckpt_every);
+    float* dst = (m == L.nseg - 1) ? u_T : L.ckpt(workspace, m + 1);
+    Fields f{L.ckpt(workspace, m), dst, kappa, src, L.tmp(workspace)};
+    st = enqueue_tuned(f, nx, ny, len, dt, bc, CPB_F32, t, s);
+    if (st != CPB_SUCCESS) return st;
+  }
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_adjoint_backward(const float* kappa, const float* src, const float* lambda_T, int nx,
+                                int ny, int steps, float dt, cpb_boundary bc, int ckpt_every,
+                                float* grad_u0, float* grad_kappa, void* workspace, size_t ws_bytes,
+                                cpb_stream_t stream) {
+  cpb_status st = adjoint_check(nx, ny, steps, dt, bc, ckpt_every, workspace, ws_bytes);
+  if (st != CPB_SUCCESS) return st;
+  if (!kappa || !lambda_T || !grad_u0 || !grad_kappa) return CPB_ERR_INVALID_VALUE;
+  const AdjointLayout L = adjoint_layout(nx, ny, steps, ckpt_every);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t nb = (size_t)nx * ny * sizeof(float);
+  CPB_TRY(cudaMemsetAsync(grad_kappa, 0, nb, s));
+  if (steps == 0) {
+    CPB_TRY(cudaMemcpyAsync(grad_u0, lambda_T, nb, cudaMemcpyDeviceToDevice, s));
+    return CPB_SUCCESS;
+  }
+  cpb_tuning t1 = lookup_tuning(nx, ny, CPB_F32, bc);
+  t1.k = 1;  // recompute one step per state
+  const float* lam_cur = lambda_T;
+  int flip = 0;
+  for (int m = L.nseg - 1; m >= 0; --m) {
+    const int len = std::min(ckpt_every, steps - m * ckpt_every);
+    // states u_{a}, u_{a+1}, ..., u_{a+len-1}: the checkpoint, then recompute
+    for (int q = 1; q < len; ++q) {
+      void* prev = q == 1 ? (void*)L.ckpt(workspace, m) : (void*)L.seg(workspace, q - 2);
+      Fields f{prev, L.seg(workspace, q - 1), kappa, src, L.tmp(workspace)};
+      st = enqueue_tuned(f, nx, ny, 1, dt, bc, CPB_F32, t1, s);
+      if (st != CPB_SUCCESS) return st;
+    }
+    for (int q = len - 1; q >= 0; --q) {
+      const float* un = q == 0 ? L.ckpt(workspace, m) : L.seg(workspace, q - 1);
+      float* out = (m == 0 && q == 0) ? grad_u0 : L.lam(workspace, flip);
+      CPB_TRY(launch_adjoint_step(lam_cur, out, un, kappa, grad_kappa, nx, ny, dt, (int)bc, s));
+      lam_cur = out;
+      flip ^= 1;
+    }
+  }
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_stencil_adjoint(const float* u0, const float* kappa, const float* src,
+                               const float* lambda_T, int nx, int ny, int steps, float dt,
+                               cpb_boundary bc, int ckpt_every, float* grad_u0, float* grad_kappa,
+                               void* workspace, size_t ws_bytes, cpb_stream_t stream) {
+  cpb_status st = adjoint_check(nx, ny, steps, dt, bc, ckpt_every, workspace, ws_bytes);
+  if (st != CPB_SUCCESS) return st;
+  const AdjointLayout L = adjoint_layout(nx, ny, steps, ckpt_every);
+  // u_T is not needed by the backward sweep: park it in a lambda slot.
+  st = cpb_adjoint_forward(u0, kappa, src, nx, ny, steps, dt, bc, ckpt_every, L.lam(workspace, 1),
+                           workspace, ws_bytes, stream);
+  if (st != CPB_SUCCESS) return st;
+  return cpb_adjoint_backward(kappa, src, lambda_T, nx, ny, steps, dt, bc, ckpt_every, grad_u0,
+                              grad_kappa, workspace, ws_bytes, stream);
 }
 
 cpb_status cpb_graph_create(void* u_in, void* u_out, const void* kappa, const void* src, int nx,

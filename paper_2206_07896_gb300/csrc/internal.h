@@ -23,7 +23,8 @@ struct StreamPass {
   int variant;      // 0: register prefetch, 1: TMA bulk-copy ring
   int stages;       // variant 1: ring slots per warp (power of two, 2..16)
   int wait_limit;   // variant 1: mbarrier polls before a wait gives up
-  int inject_row;   // variant 1, tests only: a row whose copies never complete (-1: off)
+  int inject_on;    // variant 1, tests only: 1 = the copies of row inject_row never complete
+  int inject_row;
 };
 
 // Number of output columns per warp strip for temporal depth k (128 columns
@@ -60,4 +61,20 @@ cudaError_t launch_bf16_round(const float* x, uint16_t* out, long long n, cudaSt
 cudaError_t launch_bf16k_pack(const float* u, uint32_t* st, long long n, cudaStream_t s);
 cudaError_t launch_bf16k_unpack(const uint32_t* st, float* u, long long n, cudaStream_t s);
 
+}  // namespace cpb
+
+#include "../../include/cpb.h"
+namespace cpb {
+// Batched persistent launch (k_batch.cu).
+int batch_threads_max();
+int batch_depth();
+cudaError_t batch_blocks_per_sm(int threads, int* out);
+cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
+                         int grain, int blocks, int threads, int* work, cudaStream_t s);
+}  // namespace cpb
+
+namespace cpb {
+// One adjoint step (k_adjoint.cu): lam_out = lam + dt D lam; gk += face terms.
+cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u, const float* k,
+                                float* gk, int nx, int ny, float dt, int bc, cudaStream_t s);
 }  // namespace cpb

@@ -1,0 +1,184 @@
+// Batched persistent stencil: thousands of independent grids of uneven sizes
+// and step counts in ONE launch.
+//
+// The launch is the GPU counterpart of the paper's runtime (Sec. IV): instead
+// of a host thread pool fetching blocks from a mutex-protected task queue in
+// grains of block_per_fetch ("coarse-grained fetching"), resident CTAs fetch
+// grids from a device work queue with one atomicAdd per grain of `grain`
+// grids.  The host orders the queue longest-first (LPT) so the expensive grids
+// start early.  Two queues:
+//   large grids (cells >= team_cells): a whole CTA per grid; its warps split the
+//     (strip, chunk) items of each pass and meet at __syncthreads between
+//     passes;
+//   small grids: one warp per grid, passes separated by __syncwarp.
+// Each pass is the streaming temporal-blocked routine of the single-grid path
+// (stream_item) with u read through L2 (.cg), because a grid's buffers are
+// rewritten by later passes of the same launch.  A grid's u_in is its
+// ping-pong partner (clobbered), and the pass count is made odd so the result
+// lands in u_out.  No CTA ever waits on another CTA, so there is no inter-CTA
+// wait to bound.  Invalid descriptors are skipped and reported in the status
+// word (work[2] = CPB_ERR_INVALID_VALUE).
+#include "k_stream.cuh"
+
+namespace cpb {
+namespace {
+
+constexpr int BATCH_K = 4;
+constexpr int BATCH_MAX_THREADS = 384;
+
+// Depth of pass i of a grid with S steps at depth K, with the pass count made
+// odd (split the last pass, or, if it has depth 1, the one before it).
+__device__ __forceinline__ int npasses(int S, int K) {
+  const int P = (S + K - 1) / K;
+  return (P % 2 == 0) ? P + 1 : P;
+}
+
+__device__ __forceinline__ int pass_depth(int i, int S, int K) {
+  const int P = (S + K - 1) / K;
+  const int dl = S - (P - 1) * K;  // depth of the last regular pass
+  if (P % 2 == 1) return i < P - 1 ? K : dl;
+  if (dl >= 2) {  // split the last pass
+    if (i < P - 1) return K;
+    return i == P - 1 ? dl - dl / 2 : dl / 2;
+  }
+  // dl == 1: split pass P-2 (depth K >= 2)
+  if (i < P - 2) return K;
+  if (i == P - 2) return K - K / 2;
+  if (i == P - 1) return K / 2;
+  return 1;
+}
+
+__device__ __forceinline__ bool desc_ok(const cpb_grid_desc& g) {
+  return g.nx >= 1 && g.ny >= 1 && g.steps >= 0 && g.u_in && g.u_out && g.kappa &&
+         g.u_in != g.u_out && g.dt > 0.0f;
+}
+
+// Chunk height for a team of nw warps: choose the number of chunks that best
+// balances items over warps, discounting the 2*d halo rows each chunk re-reads.
+__device__ __forceinline__ int team_chunk_rows(int ny, int strips, int nw, int d) {
+  if (nw == 1) return ny;
+  int best = ny;
+  float best_eff = -1.0f;
+  for (int c = 1; c <= 8; ++c) {
+    int chunks = (c * nw + strips - 1) / strips;
+    if (chunks > ny) chunks = ny;
+    const int rows = (ny + chunks - 1) / chunks;
+    const int items = strips * ((ny + rows - 1) / rows);
+    const int rounds = (items + nw - 1) / nw;
+    const float eff = (float)items / (float)(rounds * nw) * (float)rows / (float)(rows + 2 * d);
+    if (eff > best_eff + 1e-4f) {
+      best_eff = eff;
+      best = rows;
+    }
+  }
+  return best;
+}
+
+template <bool CTA>
+__device__ __forceinline__ void team_sync() {
+  if (CTA)
+    __syncthreads();
+  else
+    __syncwarp();
+}
+
+// Run all steps of one grid with a team: the whole CTA (CTA = true) or one warp.
+template <bool CTA>
+__device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int lane, int* status) {
+  if (!desc_ok(g)) {
+    if (lane == 0 && wib == 0) atomicExch(status, (int)CPB_ERR_INVALID_VALUE);
+    return;
+  }
+  const int nx = g.nx, ny = g.ny, S = g.steps;
+  const size_t n = (size_t)nx * ny;
+  if (S == 0) {
+    const int tid = wib * 32 + lane, nt = nw * 32;
+    for (size_t i = tid; i < n; i += nt)
+      static_cast<float*>(g.u_out)[i] = __ldcg(static_cast<const float*>(g.u_in) + i);
+    team_sync<CTA>();
+    return;
+  }
+  constexpr int HALO = (BATCH_K + 3) & ~3;
+  constexpr int OW = 128 - 2 * HALO;
+  StreamArgs a;
+  a.kappa = g.kappa;
+  a.src = g.src;
+  a.nx = nx;
+  a.ny = ny;
+  a.dt = g.dt;
+  a.hdt = 0.5f * g.dt;
+  a.bc = bc;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(g.u_in) | reinterpret_cast<uintptr_t>(g.u_out) |
+                       reinterpret_cast<uintptr_t>(g.kappa) | reinterpret_cast<uintptr_t>(g.src);
+  a.vec = (nx % 4 == 0) && (al % 16 == 0);
+  a.n_strips = (nx + OW - 1) / OW;
+  a.stages = 0;
+  a.wait_limit = 0;
+  a.inject_on = 0;
+  a.inject_row = 0;
+  const int P = npasses(S, BATCH_K);
+  const void* src_buf = g.u_in;
+  for (int i = 0; i < P; ++i) {
+    void* dst = ((P - 1 - i) % 2 == 0) ? g.u_out : g.u_in;
+    a.u_in = src_buf;
+    a.u_out = dst;
+    a.depth = pass_depth(i, S, BATCH_K);
+    a.chunk_rows = team_chunk_rows(ny, a.n_strips, nw, a.depth);
+    a.n_items = a.n_strips * ((ny + a.chunk_rows - 1) / a.chunk_rows);
+    for (int it = wib; it < a.n_items; it += nw) stream_item<BATCH_K, false, true>(a, it, lane);
+    team_sync<CTA>();
+    src_buf = dst;
+  }
+}
+
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
+    batch_kernel(const cpb_grid_desc* __restrict__ descs, const int* __restrict__ order, int ngrids,
+                 int n_large, int bc, int grain, int* work) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ int s_first;
+  // Phase 1: large grids, one CTA per grid, fetched `grain` at a time.
+  for (;;) {
+    if (threadIdx.x == 0) s_first = atomicAdd(&work[0], grain);
+    __syncthreads();
+    const int first = s_first;
+    __syncthreads();
+    if (first >= n_large) break;
+    const int last = min(first + grain, n_large);
+    for (int q = first; q < last; ++q) {
+      const cpb_grid_desc g = descs[order[q]];
+      run_grid<true>(g, bc, wib, nw, lane, &work[2]);
+    }
+  }
+  // Phase 2: small grids, one warp per grid.
+  const int n_small = ngrids - n_large;
+  for (;;) {
+    int first = 0;
+    if (lane == 0) first = atomicAdd(&work[1], grain);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first >= n_small) break;
+    const int last = min(first + grain, n_small);
+    for (int q = first; q < last; ++q) {
+      const cpb_grid_desc g = descs[order[n_large + q]];
+      run_grid<false>(g, bc, 0, 1, lane, &work[2]);
+    }
+  }
+}
+
+}  // namespace
+
+int batch_threads_max() { return BATCH_MAX_THREADS; }
+int batch_depth() { return BATCH_K; }
+
+cudaError_t batch_blocks_per_sm(int threads, int* out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_kernel, threads, 0);
+}
+
+cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
+                         int grain, int blocks, int threads, int* work, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(work, 0, 3 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  batch_kernel<<<blocks, threads, 0, s>>>(descs, order, ngrids, n_large, bc, grain, work);
+  return cudaGetLastError();
+}
+
+}  // namespace cpb

@@ -57,7 +57,8 @@ struct StreamArgs {
   int depth;       // time steps of this pass, 1..K
   int stages;      // variant 1: ring slots per warp (power of two)
   int wait_limit;  // variant 1: bounded mbarrier wait, in try_wait polls
-  int inject_row;  // variant 1, tests only: expect bytes that never arrive on this row (-1: off)
+  int inject_on;   // variant 1, tests only: 1 = the copies of row inject_row never complete
+  int inject_row;
 };
 
 #define CPB_FULL 0xffffffffu
@@ -80,6 +81,12 @@ struct Io<false> {
     return __ldg(static_cast<const float*>(p) + i);
   }
   static __device__ __forceinline__ float k1(const void* p, size_t i) { return u1(p, i); }
+  static __device__ __forceinline__ float4 u4_cg(const void* p, size_t i) {
+    return __ldcg(reinterpret_cast<const float4*>(static_cast<const float*>(p) + i));
+  }
+  static __device__ __forceinline__ float u1_cg(const void* p, size_t i) {
+    return __ldcg(static_cast<const float*>(p) + i);
+  }
   // shared-memory row slot readers (offset in cells)
   static __device__ __forceinline__ float4 su4(const unsigned char* row, int o) {
     return *reinterpret_cast<const float4*>(row + 4 * o);
@@ -108,6 +115,12 @@ struct Io<true> {
   }
   static __device__ __forceinline__ float k1(const void* p, size_t i) {
     return bf16_bits_to_f32(__ldg(static_cast<const unsigned short*>(p) + i));
+  }
+  static __device__ __forceinline__ float4 u4_cg(const void* p, size_t i) {
+    return unpack_u(__ldcg(reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(p) + i)));
+  }
+  static __device__ __forceinline__ float u1_cg(const void* p, size_t i) {
+    return kahan_value(__ldcg(static_cast<const uint32_t*>(p) + i));
   }
   static __device__ __forceinline__ float4 su4(const unsigned char* row, int o) {
     return unpack_u(*reinterpret_cast<const uint4*>(row + 4 * o));
@@ -252,14 +265,14 @@ __device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int n
 // ---------------------------------------------------------------------------
 // variant 0: register prefetch, one row ahead
 // ---------------------------------------------------------------------------
-template <int K, bool BF>
-__global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
+// One warp item (strip, chunk) of one pass.  COH: read u through L2 only
+// (ld.global.cg), for callers that read, in the same launch, a buffer they
+// wrote earlier (the batched persistent kernel); otherwise the read-only path.
+template <int K, bool BF, bool COH>
+__device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int lane) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   using IO = Io<BF>;
-  const int lane = threadIdx.x & 31;
-  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (item >= a.n_items) return;  // warp-uniform
   const int nx = a.nx, ny = a.ny, d = a.depth;
   const bool periodic = a.bc == BC_PERIODIC;
   const int strip = item % a.n_strips, chunk = item / a.n_strips;
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
       if (lc.kb == 2) k4 = f4(k4.w);
       Kp = k4;
       if (rin && lc.cin4) {
-        U = IO::u4(a.u_in, row + lc.xv);
+        U = COH ? IO::u4_cg(a.u_in, row + lc.xv) : IO::u4(a.u_in, row + lc.xv);
         S = a.src ? IO::k4(a.src, row + lc.xv) : f4(0.0f);
       } else {
         U = f4(0.0f);
@@ -291,7 +304,8 @@ __global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
       for (int e = 0; e < 4; ++e) {
         kk[e] = IO::k1(a.kappa, row + lc.xe[e]);
         bool in = rin && lc.ine[e];
-        uu[e] = in ? IO::u1(a.u_in, row + lc.xe[e]) : 0.0f;
+        uu[e] = in ? (COH ? IO::u1_cg(a.u_in, row + lc.xe[e]) : IO::u1(a.u_in, row + lc.xe[e]))
+                   : 0.0f;
         ss[e] = (in && a.src) ? IO::k1(a.src, row + lc.xe[e]) : 0.0f;
       }
       U = make_float4(uu[0], uu[1], uu[2], uu[3]);
@@ -315,6 +329,13 @@ __global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
     const int ro = r_in - d;
     if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, a.vec, out, packed);
   }
+}
+
+template <int K, bool BF>
+__global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= a.n_items) return;  // warp-uniform
+  stream_item<K, BF, false>(a, item, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -454,7 +475,7 @@ __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = 0; i < R && i < nrows; ++i)
       issue_row<BF>(a, r_first + i, x0a, ring + (size_t)i * SL::BYTES, &bars[i],
-                    (r_first + i == a.inject_row) ? 16u : 0u);
+                    (a.inject_on && r_first + i == a.inject_row) ? 16u : 0u);
   }
   __syncwarp();
 
@@ -483,7 +504,7 @@ __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
     if (lane == 0 && i + R < nrows) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue_row<BF>(a, r_in + R, x0a, ring + (size_t)slot * SL::BYTES, &bars[slot],
-                    (r_in + R == a.inject_row) ? 16u : 0u);
+                    (a.inject_on && r_in + R == a.inject_row) ? 16u : 0u);
     }
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
@@ -525,6 +546,7 @@ cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
   a.depth = p.depth;
   a.stages = p.stages;
   a.wait_limit = p.wait_limit;
+  a.inject_on = p.inject_on;
   a.inject_row = p.inject_row;
   a.n_strips = (p.nx + OW - 1) / OW;
   const long long n_chunks = (p.ny + p.chunk_rows - 1) / p.chunk_rows;
@@ -541,8 +563,11 @@ cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (shm > 48 * 1024 && dev < 32 && !(attr_done & (1u << dev))) {
-      cudaError_t e = cudaFuncSetAttribute(stream_bulk_kernel<K, BF>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      int optin = 0;
+      cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(stream_bulk_kernel<K, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin);
       if (e != cudaSuccess) return e;
       attr_done |= 1u << dev;
     }

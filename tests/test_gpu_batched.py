@@ -1,0 +1,153 @@
+"""GPU parity of the batched persistent launch (many uneven grids, one launch)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+cpb = pytest.importorskip("paper_2206_07896_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def small_batch(seed, bc):
+    rng = np.random.default_rng(seed)
+    shapes = [(1, 1), (1, 200), (200, 1), (3, 5), (128, 128), (300, 70), (64, 64), (257, 33)]
+    shapes += [(int(a), int(b)) for a, b in rng.integers(1, 260, (40, 2))]
+    steps = [int(x) for x in rng.integers(0, 26, len(shapes))]
+    steps[0], steps[1] = 0, 1
+    grids = [W.random_grid(seed * 1000 + i, nx, ny, st, bc) for i, ((nx, ny), st) in
+             enumerate(zip(shapes, steps))]
+    return grids
+
+
+def pack(grids, dev):
+    sizes = [g.nx * g.ny for g in grids]
+    off = np.zeros(len(grids), np.int64)
+    off[1:] = np.cumsum(sizes)[:-1]
+    # pad each grid start to 16 bytes so most grids take the 128-bit path
+    off = np.array([((o + 3) // 4) * 4 + 4 * i for i, o in enumerate(off)], np.int64)
+    total = int(off[-1] + sizes[-1] + 8)
+    u = torch.zeros(total, dtype=torch.float32, device=dev)
+    k = torch.ones(total, dtype=torch.float32, device=dev)
+    s = torch.zeros(total, dtype=torch.float32, device=dev)
+    for g, o in zip(grids, off):
+        n = g.nx * g.ny
+        u[o:o + n] = torch.from_numpy(g.u.reshape(-1)).to(dev)
+        k[o:o + n] = torch.from_numpy(g.kappa.reshape(-1)).to(dev)
+        s[o:o + n] = torch.from_numpy(g.src.reshape(-1)).to(dev)
+    return u, k, s, off
+
+
+def run_batch(L, grids, dev, bc, plan, u, k, s, off):
+    uo = torch.full_like(u, -1.0)
+    uin = u.clone()
+    descs = cpb.batch_descriptors(uin, uo, k, s, off, [g.nx for g in grids], [g.ny for g in grids],
+                                  [g.steps for g in grids], [g.dt for g in grids])
+    order, n_large = L.cpb_batch_order(descs, plan)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+    L.cpb_stencil_batched(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, bc, plan, work)
+    assert L.cpb_batch_status(work) == 0
+    return uo, n_large
+
+
+@pytest.mark.parametrize("bc", [W.DIRICHLET, W.PERIODIC])
+@pytest.mark.parametrize("plan", [{"grain": 1, "blocks": 0, "threads": 384, "team_cells": 4096},
+                                  {"grain": 3, "blocks": 3, "threads": 256, "team_cells": 20000},
+                                  {"grain": 2, "blocks": 0, "threads": 128, "team_cells": 1}])
+def test_batched_bit_exact(dev, bc, plan):
+    L = cpb.lib(fma=False)
+    grids = small_batch(7 + bc, bc)
+    u, k, s, off = pack(grids, dev)
+    uo, n_large = run_batch(L, grids, dev, bc, plan, u, k, s, off)
+    assert 0 < n_large < len(grids) or plan["team_cells"] == 1
+    out = uo.cpu().numpy()
+    for g, o in zip(grids, off):
+        ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, bc, "f32")
+        got = out[o:o + g.nx * g.ny].reshape(g.ny, g.nx)
+        np.testing.assert_array_equal(got, ref, err_msg=f"{g.nx}x{g.ny} steps={g.steps}")
+
+
+def test_batch_order_is_lpt_and_validates(dev):
+    L = cpb.lib(fma=False)
+    grids = small_batch(3, W.DIRICHLET)
+    u, k, s, off = pack(grids, dev)
+    descs = cpb.batch_descriptors(u, torch.empty_like(u), k, s, off, [g.nx for g in grids],
+                                  [g.ny for g in grids], [g.steps for g in grids],
+                                  [g.dt for g in grids])
+    plan = {"grain": 1, "team_cells": 4096}
+    order, n_large = L.cpb_batch_order(descs, plan)
+    assert sorted(order) == list(range(len(grids)))
+    cost = [g.nx * g.ny * g.steps for g in grids]
+    big = [i for i in order[:n_large]]
+    assert all(grids[i].nx * grids[i].ny >= 4096 for i in big)
+    assert all(cost[a] >= cost[b] for a, b in zip(big, big[1:]))
+    small = order[n_large:]
+    assert all(cost[a] >= cost[b] for a, b in zip(small, small[1:]))
+    descs[5].nx = 0
+    with pytest.raises(cpb.CpbError) as e:
+        L.cpb_batch_order(descs, plan)
+    assert e.value.status == cpb.CPB_ERR_INVALID_VALUE
+
+
+def test_batched_invalid_device_descriptor_is_reported(dev):
+    L = cpb.lib(fma=False)
+    grids = small_batch(5, W.PERIODIC)[:10]
+    u, k, s, off = pack(grids, dev)
+    uo = torch.full_like(u, -1.0)
+    descs = cpb.batch_descriptors(u.clone(), uo, k, s, off, [g.nx for g in grids],
+                                  [g.ny for g in grids], [g.steps for g in grids],
+                                  [g.dt for g in grids])
+    order, n_large = L.cpb_batch_order(descs, None)
+    descs[order[-1]].ny = -3          # corrupt only the device copy
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+    L.cpb_stencil_batched(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, W.PERIODIC, None, work)
+    assert L.cpb_batch_status(work) == cpb.CPB_ERR_INVALID_VALUE
+    out = uo.cpu().numpy()
+    for i, (g, o) in enumerate(zip(grids, off)):
+        if i == order[-1]:
+            continue
+        ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, W.PERIODIC, "f32")
+        np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref)
+
+
+def test_batched_graph_capture(dev):
+    L = cpb.lib(fma=False)
+    grids = small_batch(11, W.DIRICHLET)[:20]
+    u, k, s, off = pack(grids, dev)
+    uo = torch.zeros_like(u)
+    uin = u.clone()
+    descs = cpb.batch_descriptors(uin, uo, k, s, off, [g.nx for g in grids], [g.ny for g in grids],
+                                  [g.steps for g in grids], [g.dt for g in grids])
+    order, n_large = L.cpb_batch_order(descs, None)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+    s_ = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s_):
+        L.cpb_stencil_batched(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, W.DIRICHLET, None,
+                              work, stream=s_)
+    for _ in range(2):
+        uin.copy_(u)       # the batch clobbers u_in; restore it before each replay
+        uo.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        out = uo.cpu().numpy()
+        for g, o in zip(grids, off):
+            ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, W.DIRICHLET, "f32")
+            np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref)
