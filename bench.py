@@ -183,6 +183,186 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Other forms of the path (reported under "forms", not part of "value")
+# ---------------------------------------------------------------------------
+def _time(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def form_precision(L, cpb, dev, stream, n=16384, steps=2000):
+    """FP32 vs BF16-Kahan storage on the 16384^2 Dirichlet workload."""
+    import torch
+    g = W.precision(n=n, steps=steps)
+    nx, ny = g.nx, g.ny
+    sh = stream.cuda_stream
+    u = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy(g.src).to(dev)
+    del g
+    a, b, out = torch.empty_like(u), torch.empty_like(u), torch.empty_like(u)
+    a.copy_(u)
+    t32 = L.cpb_autotune(a, b, k, s, nx, ny, 24, 1e-4, W.DIRICHLET, cpb.CPB_F32, stream=sh)
+    dt = float(np.float32(0.2 / float(k.max())))
+    ms32 = _time(lambda: L.cpb_stencil_launch_tuned(u, out, k, s, nx, ny, steps, dt, W.DIRICHLET,
+                                                    cpb.CPB_F32, tuning=t32, scratch=a, stream=sh),
+                 2, stream)
+    ref32 = out.clone()
+    hs = torch.empty(L.cpb_heat_sum_workspace_bytes(nx, ny) // 8 + 1, dtype=torch.float64, device=dev)
+    d_sum = torch.empty((), dtype=torch.float64, device=dev)
+    ms_sum = _time(lambda: L.cpb_heat_sum(ref32, nx, ny, cpb.CPB_F32, d_sum, hs, hs.numel() * 8,
+                                          stream=sh), 3, stream)
+    # BF16-Kahan state and bf16 fields, converted on the device
+    N = nx * ny
+    st = torch.empty(N, dtype=torch.int32, device=dev)
+    kb = torch.empty(N, dtype=torch.int16, device=dev)
+    sb = torch.empty(N, dtype=torch.int16, device=dev)
+    L.cpb_bf16k_pack(u, st, N, stream=sh)
+    L.cpb_bf16_round(k, kb, N, stream=sh)
+    L.cpb_bf16_round(s, sb, N, stream=sh)
+    del a, b
+    sa, sbuf, so = torch.empty_like(st), torch.empty_like(st), torch.empty_like(st)
+    sa.copy_(st)
+    t16 = L.cpb_autotune(sa, sbuf, kb, sb, nx, ny, 24, dt, W.DIRICHLET, cpb.CPB_BF16_KAHAN, stream=sh)
+    ms16 = _time(lambda: L.cpb_stencil_launch_tuned(st, so, kb, sb, nx, ny, steps, dt, W.DIRICHLET,
+                                                    cpb.CPB_BF16_KAHAN, tuning=t16, scratch=sa,
+                                                    stream=sh), 2, stream)
+    un = torch.empty_like(u)
+    L.cpb_bf16k_unpack(so, un, N, stream=sh)
+    torch.cuda.synchronize()
+    diff = float((un - ref32).abs().max() / ref32.abs().max())
+    upd = N * steps
+    hbm, _ = peaks()
+    return {"workload": f"precision-{n}x{n}-dirichlet-{steps}steps",
+            "f32": {"gcells": upd / ms32 / 1e6, "ms": ms32, "tuning": t32,
+                    "effective_gbs_16B": upd * 16 / t32["k"] / ms32 / 1e6},
+            "bf16_kahan": {"gcells": upd / ms16 / 1e6, "ms": ms16, "tuning": t16,
+                           "effective_gbs_12B": upd * 12 / t16["k"] / ms16 / 1e6,
+                           "rel_linf_vs_f32_gpu": diff},
+            "speedup_bf16_vs_f32": ms32 / ms16,
+            "heat_sum_fp64": {"ms": ms_sum, "gbs": N * 4 / ms_sum / 1e6, "frac_hbm": N * 4 / ms_sum / 1e6 / hbm},
+            "note": "error vs the FP64 oracle is measured in tests/test_gpu_precision.py"}
+
+
+def form_batched(L, cpb, dev, stream, ngrids=4096):
+    """4096 uneven grids in one persistent launch vs one tuned launch sequence per grid."""
+    import ctypes as C
+    import torch
+    bt = W.batching(ngrids=ngrids)
+    sh = stream.cuda_stream
+    # pad each grid to a 16-byte boundary so the 128-bit path applies where nx % 4 == 0
+    cells = (bt.nx.astype(np.int64) * bt.ny.astype(np.int64))
+    off = np.zeros(bt.ngrids, np.int64)
+    off[1:] = np.cumsum((cells + 3) // 4 * 4)[:-1]
+    total = int(off[-1] + cells[-1])
+    u = torch.empty(total, dtype=torch.float32, device=dev)
+    k = torch.ones(total, dtype=torch.float32, device=dev)
+    s = torch.zeros(total, dtype=torch.float32, device=dev)
+    hu, hk, hs = (torch.from_numpy(x) for x in (bt.u, bt.kappa, bt.src))
+    # bulk copy, then scatter to the padded layout on the device
+    du, dk, ds = hu.to(dev), hk.to(dev), hs.to(dev)
+    src_idx = torch.from_numpy(np.concatenate([np.arange(int(bt.offset[g]), int(bt.offset[g] + cells[g]))
+                                               for g in range(bt.ngrids)])).to(dev)
+    dst_idx = torch.from_numpy(np.concatenate([np.arange(int(off[g]), int(off[g] + cells[g]))
+                                               for g in range(bt.ngrids)])).to(dev)
+    u[dst_idx] = du[src_idx]
+    k[dst_idx] = dk[src_idx]
+    s[dst_idx] = ds[src_idx]
+    del du, dk, ds, src_idx, dst_idx
+    uin, uo = u.clone(), torch.empty_like(u)
+    descs = cpb.batch_descriptors(uin, uo, k, s, off, bt.nx, bt.ny, bt.steps, bt.dt)
+    plan = L.cpb_batch_plan_default()
+    order, n_large = L.cpb_batch_order(descs, plan)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+
+    def run_batch():
+        uin.copy_(u)
+        L.cpb_stencil_batched(d_descs, d_order, bt.ngrids, n_large, cpb.CPB_F32, W.DIRICHLET, plan,
+                              work, stream=sh)
+
+    def run_copy_only():
+        uin.copy_(u)
+
+    ms_total = _time(run_batch, 3, stream)
+    ms_copy = _time(run_copy_only, 3, stream)
+    ms_b = ms_total - ms_copy
+    status = L.cpb_batch_status(work, stream=sh)
+    upd = bt.updates
+    # one-grid-at-a-time baseline (tuned single-grid path, one call per grid)
+    scratch = torch.empty(int(cells.max()), dtype=torch.float32, device=dev)
+
+    def run_each():
+        for gi in range(bt.ngrids):
+            o, c = int(off[gi]), int(cells[gi])
+            L.cpb_stencil_launch_tuned(u[o:o + c], uo[o:o + c], k[o:o + c], s[o:o + c], int(bt.nx[gi]),
+                                       int(bt.ny[gi]), int(bt.steps[gi]), float(bt.dt[gi]), W.DIRICHLET,
+                                       cpb.CPB_F32, tuning=None, scratch=scratch[:c], stream=sh)
+
+    ms_each = _time(run_each, 1, stream)
+    return {"workload": f"batch-{bt.ngrids}-grids-32..1024-steps-10..500", "updates": upd,
+            "cells": int(cells.sum()), "n_large": n_large, "plan": plan,
+            "batched": {"gcells": upd / ms_b / 1e6, "ms": ms_b, "status": status},
+            "one_grid_at_a_time": {"gcells": upd / ms_each / 1e6, "ms": ms_each},
+            "speedup_batched_vs_per_grid": ms_each / ms_b}
+
+
+def form_adjoint(L, cpb, dev, stream):
+    """Gradient of 0.5||u_T - target||^2 w.r.t. u0 and kappa, 2048^2, 200 steps, ckpt 20."""
+    import torch
+    g = W.differentiation()
+    sh = stream.cuda_stream
+    nx, ny, T, ck = g.nx, g.ny, g.steps, g.extras["ckpt"]
+    u0 = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    tgt = torch.from_numpy(g.extras["target"]).to(dev)
+    wsb = L.cpb_adjoint_workspace_bytes(nx, ny, T, ck)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    uT, gu, gk = torch.empty_like(u0), torch.empty_like(u0), torch.empty_like(u0)
+    fwd_out, scr = torch.empty_like(u0), torch.empty_like(u0)
+    ms_fwd = _time(lambda: L.cpb_stencil_launch_tuned(u0, fwd_out, k, None, nx, ny, T, float(g.dt),
+                                                      g.bc, cpb.CPB_F32, scratch=scr, stream=sh),
+                   3, stream)
+
+    def grad():
+        L.cpb_adjoint_forward(u0, k, None, nx, ny, T, float(g.dt), g.bc, ck, uT, ws, wsb, stream=sh)
+        lam = uT - tgt
+        L.cpb_adjoint_backward(k, None, lam, nx, ny, T, float(g.dt), g.bc, ck, gu, gk, ws, wsb,
+                               stream=sh)
+
+    ms_grad = _time(grad, 3, stream)
+    upd = nx * ny * T
+    return {"workload": g.name, "forward": {"gcells": upd / ms_fwd / 1e6, "ms": ms_fwd},
+            "gradient": {"ms": ms_grad, "gcells_equiv": upd / ms_grad / 1e6,
+                         "ratio_to_forward": ms_grad / ms_fwd},
+            "fd_cost_per_direction_ms": 2 * ms_fwd,
+            "note": "one gradient = forward with checkpoints + recompute + adjoint sweep; "
+                    "central FD needs 2 forwards per direction"}
+
+
+def measure_forms(L, cpb, dev, stream):
+    out = {}
+    for name, fn in (("precision", form_precision), ("batched", form_batched),
+                     ("adjoint", form_adjoint)):
+        try:
+            out[name] = fn(L, cpb, dev, stream)
+        except Exception as e:  # report, never lose the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        import torch
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -311,7 +491,7 @@ def run_ours(args):
                "ms_per_step": e2e_s * 1e3}
         del hws
 
-    forms = None
+    forms = measure_forms(L, cpb, dev, stream) if (args.forms and rank == 0) else None
 
     if rank == 0:
         cpu = None
@@ -349,7 +529,8 @@ def main(argv=None):
     ap.add_argument("--wpb", type=int, default=4)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel, if measured")
-    ap.add_argument("--forms", action="store_true")
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the BF16 / batched / adjoint forms")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

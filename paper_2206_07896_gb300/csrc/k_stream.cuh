@@ -268,12 +268,14 @@ __device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int n
 // One warp item (strip, chunk) of one pass.  COH: read u through L2 only
 // (ld.global.cg), for callers that read, in the same launch, a buffer they
 // wrote earlier (the batched persistent kernel); otherwise the read-only path.
-template <int K, bool BF, bool COH>
+// FULL: the pass depth is K (known at compile time, so the per-level depth
+// guards fold away); otherwise the depth a.depth <= K is read at run time.
+template <int K, bool BF, bool COH, bool FULL = false>
 __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int lane) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   using IO = Io<BF>;
-  const int nx = a.nx, ny = a.ny, d = a.depth;
+  const int nx = a.nx, ny = a.ny, d = FULL ? K : a.depth;
   const bool periodic = a.bc == BC_PERIODIC;
   const int strip = item % a.n_strips, chunk = item / a.n_strips;
   const int xo = strip * OW;
@@ -335,7 +337,10 @@ template <int K, bool BF>
 __global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
   const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (item >= a.n_items) return;  // warp-uniform
-  stream_item<K, BF, false>(a, item, threadIdx.x & 31);
+  if (a.depth == K)
+    stream_item<K, BF, false, true>(a, item, threadIdx.x & 31);
+  else
+    stream_item<K, BF, false, false>(a, item, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -442,20 +447,18 @@ __device__ __forceinline__ void issue_row(const StreamArgs& a, int r, int x0a, u
   }
 }
 
-template <int K, bool BF>
-__global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
+template <int K, bool BF, bool FULL>
+__device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* smem) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   using SL = Slot<BF>;
   using IO = Io<BF>;
-  extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int R = a.stages;
   unsigned char* ring = smem + (size_t)wib * R * SL::BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)(blockDim.x >> 5) * R * SL::BYTES) + wib * R;
   const int item = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (item >= a.n_items) return;  // warp-uniform; no block-level barrier is used
-  const int nx = a.nx, ny = a.ny, d = a.depth;
+  const int nx = a.nx, ny = a.ny, d = FULL ? K : a.depth;
   const bool periodic = a.bc == BC_PERIODIC;
   const int strip = item % a.n_strips, chunk = item / a.n_strips;
   const int x0 = strip * OW - HALO;
@@ -522,6 +525,17 @@ __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
       mbar_wait_bounded(&bars[j & (R - 1)], (uint32_t)(j / R) & 1u, a.wait_limit);
     __syncwarp();
   }
+}
+
+template <int K, bool BF>
+__global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= a.n_items) return;  // warp-uniform; no block-level barrier is used
+  if (a.depth == K)
+    bulk_item<K, BF, true>(a, smem);
+  else
+    bulk_item<K, BF, false>(a, smem);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,128 @@
+"""Accuracy of the GPU path against the FP64 oracle, and full-size parity checks.
+
+* FP32 (default build, FMA contraction) within relative L-inf 1e-5 of FP64
+  after 1000 steps on the 8192^2 periodic workload, and after 2000 steps on the
+  precision workload's distributions.
+* BF16-Kahan storage within 1e-2 of FP64 (error reported both against the
+  original FP32 inputs and against the bf16-quantised inputs).
+* Full-size launches in the benchmark's configuration: sampled cells equal the
+  oracle's dependency-cone values bit for bit (--fmad=false build).
+* Heat conservation at full size (periodic, s = 0) with the FP64 heat sum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+cpb = pytest.importorskip("paper_2206_07896_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def rel_linf(a, ref):
+    return float(np.max(np.abs(a - ref)) / np.max(np.abs(ref)))
+
+
+def run(L, g, dev, tuning=None, steps=None):
+    u, k, s = (torch.from_numpy(x).to(dev) for x in (g.u, g.kappa, g.src))
+    out, scr = torch.empty_like(u), torch.empty_like(u)
+    L.cpb_stencil_launch_tuned(u, out, k, s, g.nx, g.ny, g.steps if steps is None else steps,
+                               float(g.dt), g.bc, cpb.CPB_F32, tuning=tuning, scratch=scr)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def sample_idx(nx, ny, count=48, seed=0):
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1), (nx // 2, 0), (0, ny // 2),
+           (nx - 1, ny // 2), (nx // 2, ny - 1), (119, 7), (120, 8), (121, 9), (nx - 121, ny - 2)]
+    pts += [(int(a), int(b)) for a, b in zip(rng.integers(0, nx, count), rng.integers(0, ny, count))]
+    return np.array([j * nx + i for i, j in pts], np.int64)
+
+
+def test_fp32_plain_scale_1000_steps_within_1e5(dev):
+    g = W.plain_scale()                     # 8192^2, periodic, 1000 steps
+    got = run(cpb.lib(fma=True), g, dev)
+    ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, g.bc, "f64", pool=oracle.host_cores())
+    err = rel_linf(got, ref)
+    print(f"plain_scale FP32 rel L-inf vs FP64 after 1000 steps: {err:.3e}")
+    assert err <= 1e-5
+
+
+def test_fp32_and_bf16k_precision_distributions_2000_steps(dev):
+    g = W.precision(n=1024, steps=2000)     # the 16384^2 workload's distributions, smaller grid
+    pool = oracle.host_cores()
+    ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, g.bc, "f64", pool=pool)
+    got32 = run(cpb.lib(fma=True), g, dev)
+    e32 = rel_linf(got32, ref)
+    # BF16-Kahan on the device from the FP32 fields
+    L = cpb.lib(fma=True)
+    N = g.nx * g.ny
+    u, k, s = (torch.from_numpy(x).to(dev) for x in (g.u, g.kappa, g.src))
+    st = torch.empty(N, dtype=torch.int32, device=dev)
+    kb = torch.empty(N, dtype=torch.int16, device=dev)
+    sb = torch.empty(N, dtype=torch.int16, device=dev)
+    L.cpb_bf16k_pack(u, st, N)
+    L.cpb_bf16_round(k, kb, N)
+    L.cpb_bf16_round(s, sb, N)
+    out, scr = torch.empty_like(st), torch.empty_like(st)
+    L.cpb_stencil_launch_tuned(st, out, kb, sb, g.nx, g.ny, g.steps, float(g.dt), g.bc,
+                               cpb.CPB_BF16_KAHAN, scratch=scr)
+    torch.cuda.synchronize()
+    got16 = oracle.bf16k_value(out.cpu().numpy().view(np.uint32)).reshape(g.ny, g.nx)
+    e16 = rel_linf(got16, ref)
+    kq = oracle.bf16_to_f32(kb.cpu().numpy().view(np.uint16)).reshape(g.ny, g.nx)
+    sq = oracle.bf16_to_f32(sb.cpu().numpy().view(np.uint16)).reshape(g.ny, g.nx)
+    u0q = oracle.bf16k_value(st.cpu().numpy().view(np.uint32)).reshape(g.ny, g.nx)
+    refq = oracle.direct(u0q, kq, sq, g.steps, g.dt, g.bc, "f64", pool=pool)
+    e16q = rel_linf(got16, refq)
+    print(f"precision 1024^2 x 2000: FP32 {e32:.3e}  BF16-Kahan {e16:.3e} "
+          f"(vs FP64 on quantised inputs {e16q:.3e})")
+    assert e32 <= 1e-5
+    assert e16 <= 1e-2
+    assert e16q <= 1e-3
+
+
+@pytest.mark.parametrize("which", ["plain_scale", "precision"])
+def test_full_size_sampled_bit_exact(dev, which):
+    L = cpb.lib(fma=False)
+    if which == "plain_scale":
+        g = W.plain_scale(steps=12)
+    else:
+        g = W.precision(steps=12)
+    nx, ny = g.nx, g.ny
+    u, k, s = (torch.from_numpy(x).to(dev) for x in (g.u, g.kappa, g.src))
+    a, b = torch.empty_like(u), torch.empty_like(u)
+    a.copy_(u)
+    best = L.cpb_autotune(a, b, k, s, nx, ny, 24, float(g.dt), g.bc, cpb.CPB_F32)
+    out, scr = torch.empty_like(u), torch.empty_like(u)
+    L.cpb_stencil_launch_tuned(u, out, k, s, nx, ny, g.steps, float(g.dt), g.bc, cpb.CPB_F32,
+                               tuning=best, scratch=scr)
+    torch.cuda.synchronize()
+    idx = sample_idx(nx, ny)
+    got = out.reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    ref = oracle.sample(g.u, g.kappa, g.src, g.steps, g.dt, g.bc, idx, "f32")
+    np.testing.assert_array_equal(got, ref)
+    assert L.cpb_device_status() == 0
+
+
+def test_full_size_conservation(dev):
+    g = W.plain_scale(zero_source=True)     # 8192^2, periodic, s = 0, 1000 steps
+    L = cpb.lib(fma=True)
+    u0 = torch.from_numpy(g.u).to(dev)
+    out = cpb.stencil(u0, torch.from_numpy(g.kappa).to(dev), None, g.steps, float(g.dt), g.bc,
+                      library=L)
+    s0, s1 = float(cpb.heat_sum(u0, library=L)), float(cpb.heat_sum(out, library=L))
+    drift = abs(s1 - s0) / abs(s0)
+    print(f"heat drift after 1000 steps (FP32 storage, FP64 sum): {drift:.3e}")
+    assert abs(s0 - oracle.heat_sum_f32(g.u)) <= g.u.size * 2.0 ** -52
+    assert drift <= 1e-6
