@@ -541,6 +541,11 @@ __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+namespace {
+// Per (storage, depth) kernel: devices on which the shared-memory opt-in was set.
+unsigned g_bulk_attr_done[2][9];
+}  // namespace
+
 template <int K, bool BF>
 cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
   constexpr int HALO = (K + 3) & ~3;
@@ -573,17 +578,20 @@ cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
   if (p.variant == 1) {
     const size_t shm = bulk_smem_bytes(BF, wpb, p.stages);
     // Opt in to more than 48 KB of dynamic shared memory, once per device.
-    static unsigned attr_done = 0;  // bit per device ordinal (< 32)
+    // The flag has internal linkage (one per translation unit and library):
+    // a function-local static of a template would be merged across every
+    // shared object loaded in the process.
+    unsigned& attr_done = g_bulk_attr_done[BF ? 1 : 0][K];  // bit per device ordinal (< 32)
     int dev = 0;
     cudaGetDevice(&dev);
-    if (shm > 48 * 1024 && dev < 32 && !(attr_done & (1u << dev))) {
+    if (shm > 48 * 1024 && (dev >= 32 || !(attr_done & (1u << dev)))) {
       int optin = 0;
       cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       if (e != cudaSuccess) return e;
       e = cudaFuncSetAttribute(stream_bulk_kernel<K, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
       if (e != cudaSuccess) return e;
-      attr_done |= 1u << dev;
+      if (dev < 32) attr_done |= 1u << dev;
     }
     stream_bulk_kernel<K, BF><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
   } else {
