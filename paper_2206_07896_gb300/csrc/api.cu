@@ -68,9 +68,9 @@ bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 bool tuning_valid(const cpb_tuning& t) {
   if (t.k < 1 || t.k > 8 || t.chunk_rows < 1 || t.warps_per_block < 1 || t.warps_per_block > 8)
     return false;
-  if (t.variant == 0) return true;
+  if (t.variant == 0) return stream_smem_bytes(true, t.k, t.warps_per_block, 0, 0) <= 227 * 1024;
   return t.variant == 1 && pow2(t.stages) && t.stages >= 2 && t.stages <= 16 &&
-         bulk_smem_bytes(false, t.warps_per_block, t.stages) <= 227 * 1024;
+         stream_smem_bytes(false, t.k, t.warps_per_block, 1, t.stages) <= 227 * 1024;
 }
 
 // Variant 1 (TMA bulk-copy ring) needs aligned rows; otherwise variant 0 runs.

@@ -84,7 +84,8 @@ __device__ __forceinline__ void team_sync() {
 
 // Run all steps of one grid with a team: the whole CTA (CTA = true) or one warp.
 template <bool CTA>
-__device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int lane, int* status) {
+__device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int lane, int* status,
+                         float4* face) {
   if (!desc_ok(g)) {
     if (lane == 0 && wib == 0) atomicExch(status, (int)CPB_ERR_INVALID_VALUE);
     return;
@@ -125,7 +126,8 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
     a.depth = pass_depth(i, S, BATCH_K);
     a.chunk_rows = team_chunk_rows(ny, a.n_strips, nw, a.depth);
     a.n_items = a.n_strips * ((ny + a.chunk_rows - 1) / a.chunk_rows);
-    for (int it = wib; it < a.n_items; it += nw) stream_item<BATCH_K, false, true>(a, it, lane);
+    for (int it = wib; it < a.n_items; it += nw)
+      stream_item<BATCH_K, false, true>(a, it, lane, face);
     team_sync<CTA>();
     src_buf = dst;
   }
@@ -136,6 +138,9 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
                  int n_large, int bc, int grain, int* work) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ int s_first;
+  extern __shared__ __align__(128) unsigned char smem[];
+  // this warp's ring of per-row face terms (see Pipe in k_stream.cuh)
+  float4* face = reinterpret_cast<float4*>(smem + (size_t)wib * face_ring_rows(BATCH_K) * FACE_SLOT_BYTES);
   // Phase 1: large grids, one CTA per grid, fetched `grain` at a time.
   for (;;) {
     if (threadIdx.x == 0) s_first = atomicAdd(&work[0], grain);
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
     const int last = min(first + grain, n_large);
     for (int q = first; q < last; ++q) {
       const cpb_grid_desc g = descs[order[q]];
-      run_grid<true>(g, bc, wib, nw, lane, &work[2]);
+      run_grid<true>(g, bc, wib, nw, lane, &work[2], face);
     }
   }
   // Phase 2: small grids, one warp per grid.
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
     const int last = min(first + grain, n_small);
     for (int q = first; q < last; ++q) {
       const cpb_grid_desc g = descs[order[n_large + q]];
-      run_grid<false>(g, bc, 0, 1, lane, &work[2]);
+      run_grid<false>(g, bc, 0, 1, lane, &work[2], face);
     }
   }
 }
@@ -169,15 +174,25 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
 int batch_threads_max() { return BATCH_MAX_THREADS; }
 int batch_depth() { return BATCH_K; }
 
+namespace {
+unsigned g_batch_attr_done;
+size_t batch_smem(int threads) { return (size_t)(threads / 32) * face_ring_rows(BATCH_K) * FACE_SLOT_BYTES; }
+}  // namespace
+
 cudaError_t batch_blocks_per_sm(int threads, int* out) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_kernel, threads, 0);
+  cudaError_t e = ensure_smem_optin((const void*)batch_kernel, g_batch_attr_done, batch_smem(threads));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_kernel, threads, batch_smem(threads));
 }
 
 cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
                          int grain, int blocks, int threads, int* work, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(work, 0, 3 * sizeof(int), s);
+  const size_t shm = batch_smem(threads);
+  cudaError_t e = ensure_smem_optin((const void*)batch_kernel, g_batch_attr_done, shm);
   if (e != cudaSuccess) return e;
-  batch_kernel<<<blocks, threads, 0, s>>>(descs, order, ngrids, n_large, bc, grain, work);
+  e = cudaMemsetAsync(work, 0, 3 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  batch_kernel<<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, work);
   return cudaGetLastError();
 }
 

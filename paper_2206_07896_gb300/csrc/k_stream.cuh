@@ -132,6 +132,11 @@ struct Io<true> {
 
 __device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
 
+template <bool B>
+struct Bool {
+  static constexpr bool value = B;
+};
+
 // Column geometry of one lane's 4 cells inside its strip.
 struct LaneCols {
   int xs;       // first column (unwrapped), multiple of 4
@@ -163,39 +168,66 @@ __device__ __forceinline__ LaneCols lane_cols(int xs, int nx, bool periodic) {
   return c;
 }
 
-// The K-level register pipeline of one warp strip.  At the start of the
-// iteration that receives input row r_in:
-//   W[t][0], W[t][1] = level-t rows r_in-t-2, r_in-t-1   (t = 0..K-1)
-//   FE[q] = faceE(r_in-1-q), DS[q] = dt*s(r_in-1-q), FN[q] = faceN(r_in-2-q)
-//   kprev = kappa(r_in-1)
+// Per-lane ring of the time-invariant per-row terms, in shared memory: for
+// each of `rf` row slots, the lane's faceE (kc + kE of its 4 cells), faceN
+// (kc + kN) and dt*s, as float4s.  Each lane reads only what it wrote itself,
+// so program order is the only ordering needed.  Layout per warp:
+// [slot][field][lane] float4, field 0 = faceE, 1 = faceN, 2 = dt*s.
+constexpr int FACE_FE = 0, FACE_FN = 1, FACE_DS = 2;
+constexpr int FACE_SLOT_BYTES = 3 * 32 * 16;
+
+__host__ __device__ constexpr int face_ring_rows(int k) { return k + 2; }
+
+// The K-level pipeline of one warp strip.  At the start of the iteration that
+// receives input row r_in, for level t = 0..K-1 the two rows r_in-t-2 and
+// r_in-t-1 are held in W[t][0..1] with roles that alternate between even and
+// odd iterations (ODD), so advancing the window needs no register copies.
+// The ring holds faceE / dt*s of rows >= r_in-K and faceN of rows >= r_in-K-1.
 template <int K, bool BF>
 struct Pipe {
-  float4 W[K][2], FE[K], DS[K], FN[K], kprev;
+  float4 W[K][2];
+  float4 kprev;
+  float4* ring;  // this lane's slice: ring[(slot * 3 + field) * 32]
+  int rf, slot_in;
 
-  __device__ __forceinline__ void init() {
+  __device__ __forceinline__ void init(float4* warp_ring, int lane) {
 #pragma unroll
-    for (int t = 0; t < K; ++t) W[t][0] = W[t][1] = FE[t] = DS[t] = FN[t] = f4(0.0f);
+    for (int t = 0; t < K; ++t) W[t][0] = W[t][1] = f4(0.0f);
     kprev = f4(0.0f);
+    ring = warp_ring + lane;
+    rf = face_ring_rows(K);
+    slot_in = 0;
+    for (int i = 0; i < 3 * rf; ++i) ring[i * 32] = f4(0.0f);
+  }
+
+  __device__ __forceinline__ float4& at(int slot, int field) { return ring[(slot * 3 + field) * 32]; }
+  __device__ __forceinline__ int back(int t) const {
+    int sl = slot_in - t;
+    return sl < 0 ? sl + rf : sl;
   }
 
   // Consume input row r_in; leaves level d's row r_in - d in `out` (and, for
-  // BF16-Kahan storage, its packed words in `packed`).
+  // BF16-Kahan storage, its packed words in `packed`).  FULL: d == K.
+  template <bool ODD, bool FULL>
   __device__ __forceinline__ void step(int r_in, int d, int ny, bool periodic, const LaneCols& lc,
                                        float dt, float hdt, float4 un, float4 kn, float4 sn,
                                        float4& out, uint4& packed) {
+    constexpr int S_ = ODD ? 1 : 0, C_ = ODD ? 0 : 1;
     const float4 fn_new = make_float4(kprev.x + kn.x, kprev.y + kn.y, kprev.z + kn.z, kprev.w + kn.w);
     const float kx_e = __shfl_down_sync(CPB_FULL, kn.x, 1);
-    const float4 fe_new = make_float4(kn.x + kn.y, kn.y + kn.z, kn.z + kn.w, kn.w + kx_e);
-    const float4 ds_new = make_float4(dt * sn.x, dt * sn.y, dt * sn.z, dt * sn.w);
+    at(slot_in, FACE_FE) = make_float4(kn.x + kn.y, kn.y + kn.z, kn.z + kn.w, kn.w + kx_e);
+    at(slot_in, FACE_DS) = make_float4(dt * sn.x, dt * sn.y, dt * sn.z, dt * sn.w);
+    at(back(1), FACE_FN) = fn_new;
 
     float4 nw = un;  // the row level t-1 produced in this iteration
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
-      if (t <= d) {
+      if (FULL || t <= d) {
         const int rho = r_in - t;
-        const float4 C = W[t - 1][1], S = W[t - 1][0], N = nw;
-        const float4 fe = FE[t - 1], ds = DS[t - 1], fs = FN[t - 1];
-        const float4 fn = (t == 1) ? fn_new : FN[t - 2];
+        const int sl = back(t), sls = back(t + 1);
+        const float4 C = W[t - 1][C_], S = W[t - 1][S_], N = nw;
+        const float4 fe = at(sl, FACE_FE), ds = at(sl, FACE_DS), fs = at(sls, FACE_FN);
+        const float4 fn = (t == 1) ? fn_new : at(sl, FACE_FN);
         const float uWx = __shfl_up_sync(CPB_FULL, C.w, 1);
         const float uEw = __shfl_down_sync(CPB_FULL, C.x, 1);
         const float fWx = __shfl_up_sync(CPB_FULL, fe.w, 1);
@@ -217,22 +249,13 @@ struct Pipe {
           v.z = lc.ine[2] ? v.z : 0.0f;
           v.w = lc.ine[3] ? v.w : 0.0f;
         }
-        W[t - 1][0] = W[t - 1][1];
-        W[t - 1][1] = nw;
+        W[t - 1][S_] = nw;  // becomes the centre row; the old centre becomes south
         nw = v;
       }
     }
     out = nw;
-#pragma unroll
-    for (int q = K - 1; q > 0; --q) {
-      FE[q] = FE[q - 1];
-      DS[q] = DS[q - 1];
-      FN[q] = FN[q - 1];
-    }
-    FE[0] = fe_new;
-    DS[0] = ds_new;
-    FN[0] = fn_new;
     kprev = kn;
+    slot_in = (slot_in + 1 == rf) ? 0 : slot_in + 1;
   }
 };
 
@@ -271,7 +294,7 @@ __device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int n
 // FULL: the pass depth is K (known at compile time, so the per-level depth
 // guards fold away); otherwise the depth a.depth <= K is read at run time.
 template <int K, bool BF, bool COH, bool FULL = false>
-__device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int lane) {
+__device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int lane, float4* face_ring) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   using IO = Io<BF>;
@@ -317,30 +340,39 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
   };
 
   Pipe<K, BF> pipe;
-  pipe.init();
-  int r_in = y0 - d;
+  pipe.init(face_ring, lane);
   const int r_end = y1 + d;
   float4 pu, pk, ps;
-  load_row(r_in, pu, pk, ps);
-  for (; r_in < r_end; ++r_in) {
+  load_row(y0 - d, pu, pk, ps);
+  auto body = [&](auto odd, int r_in) {
     const float4 un = pu, kn = pk, sn = ps;
     if (r_in + 1 < r_end) load_row(r_in + 1, pu, pk, ps);
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
-    pipe.step(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn, sn, out, packed);
+    pipe.template step<decltype(odd)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn, sn,
+                                                   out, packed);
     const int ro = r_in - d;
     if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, a.vec, out, packed);
+  };
+  int r_in = y0 - d;
+  for (; r_in + 1 < r_end; r_in += 2) {  // unrolled by 2: level rows alternate roles
+    body(Bool<false>{}, r_in);
+    body(Bool<true>{}, r_in + 1);
   }
+  if (r_in < r_end) body(Bool<false>{}, r_in);
 }
 
 template <int K, bool BF>
 __global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
-  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int wib = threadIdx.x >> 5;
+  const int item = blockIdx.x * (blockDim.x >> 5) + wib;
   if (item >= a.n_items) return;  // warp-uniform
+  float4* face = reinterpret_cast<float4*>(smem + (size_t)wib * face_ring_rows(K) * FACE_SLOT_BYTES);
   if (a.depth == K)
-    stream_item<K, BF, false, true>(a, item, threadIdx.x & 31);
+    stream_item<K, BF, false, true>(a, item, threadIdx.x & 31, face);
   else
-    stream_item<K, BF, false, false>(a, item, threadIdx.x & 31);
+    stream_item<K, BF, false, false>(a, item, threadIdx.x & 31, face);
 }
 
 // ---------------------------------------------------------------------------
@@ -404,46 +436,72 @@ struct Slot {
   static constexpr int S_OFF = SW * (UB + KB);
 };
 
-// Issue the copies of input row r into a slot (all completing on one
-// mbarrier); extra_bytes > 0 (tests only) expects bytes that never arrive.
-// Columns: Dirichlet copies the in-grid part of [x0a, x0a+SW) (ghost cells
-// are masked by the reader); periodic wraps, which takes two copies when the
-// window crosses an edge (nx >= SW guarantees at most two).  u and s are
-// skipped on a Dirichlet ghost row; kappa comes from the clamped row.
+// Per-lane part of the copy plan of a strip's rows.  A row takes up to six
+// bulk copies (kappa, u, s) x (one or two column pieces); lane j < 6 owns copy
+// j: field j % 3 (0 = kappa, 1 = u, 2 = s), piece j / 3.  Columns: Dirichlet
+// copies the in-grid part of [x0a, x0a+SW) (ghost cells are masked by the
+// reader); periodic wraps, which takes two pieces when the window crosses an
+// edge (nx >= SW guarantees at most two).  The row-independent part is
+// computed once per item.
+struct CopyPlan {
+  bool active;          // this lane owns a copy (piece exists, field present)
+  int field;            // 0 kappa, 1 u, 2 s
+  const unsigned char* src_base;
+  int col;              // first grid column of the piece
+  int dst_off;          // byte offset in the slot
+  uint32_t bytes;       // bytes of this copy
+  uint32_t kappa_bytes, us_bytes;  // per row: kappa bytes, u+s bytes (for expect_tx)
+};
+
 template <bool BF>
-__device__ __forceinline__ void issue_row(const StreamArgs& a, int r, int x0a, unsigned char* slot,
-                                          uint64_t* bar, uint32_t extra_bytes) {
+__device__ __forceinline__ CopyPlan make_copy_plan(const StreamArgs& a, int x0a, int lane) {
   using SL = Slot<BF>;
-  const int nx = a.nx, ny = a.ny;
-  const bool periodic = a.bc == BC_PERIODIC;
-  const bool rin = periodic || (r >= 0 && r < ny);
-  const int rr = periodic ? wrap_index(r, ny) : clamp_index(r, ny);
-  const size_t row = (size_t)rr * nx;
+  const int nx = a.nx;
   int pc[2], pw[2], po[2], np;
-  if (periodic) {
+  if (a.bc == BC_PERIODIC) {
     const int c = wrap_index(x0a, nx);
     const int w1 = min(SL::SW, nx - c);
     pc[0] = c, pw[0] = w1, po[0] = 0, np = 1;
-    if (w1 < SL::SW) pc[1] = 0, pw[1] = SL::SW - w1, po[1] = w1, np = 2;
+    pc[1] = 0, pw[1] = SL::SW - w1, po[1] = w1;
+    if (w1 < SL::SW) np = 2;
   } else {
     const int lo = max(x0a, 0), hi = min(x0a + SL::SW, nx);
     pc[0] = lo, pw[0] = hi - lo, po[0] = lo - x0a, np = 1;
+    pc[1] = pw[1] = po[1] = 0;
   }
-  const uint32_t per_cell = SL::KB + (rin ? SL::UB + (a.src ? SL::KB : 0) : 0);
-  uint32_t total = 0;
-  for (int i = 0; i < np; ++i) total += (uint32_t)pw[i] * per_cell;
-  mbar_arrive_expect_tx(bar, total + extra_bytes);
-  for (int i = 0; i < np; ++i) {
-    const size_t g = row + pc[i];
-    bulk_g2s(slot + SL::K_OFF + po[i] * SL::KB,
-             static_cast<const unsigned char*>(a.kappa) + g * SL::KB, pw[i] * SL::KB, bar);
-    if (rin) {
-      bulk_g2s(slot + po[i] * SL::UB, static_cast<const unsigned char*>(a.u_in) + g * SL::UB,
-               pw[i] * SL::UB, bar);
-      if (a.src)
-        bulk_g2s(slot + SL::S_OFF + po[i] * SL::KB,
-                 static_cast<const unsigned char*>(a.src) + g * SL::KB, pw[i] * SL::KB, bar);
-    }
+  CopyPlan p;
+  const int piece = lane / 3;
+  p.field = lane % 3;
+  p.active = lane < 6 && piece < np && !(p.field == 2 && a.src == nullptr);
+  const int pcs = piece < 2 ? piece : 0;
+  const int eb = p.field == 1 ? SL::UB : SL::KB;
+  p.src_base = static_cast<const unsigned char*>(p.field == 0 ? a.kappa : (p.field == 1 ? a.u_in : a.src));
+  p.col = pc[pcs];
+  p.dst_off = (p.field == 0 ? SL::K_OFF : (p.field == 1 ? 0 : SL::S_OFF)) + po[pcs] * eb;
+  p.bytes = (uint32_t)pw[pcs] * eb;
+  const uint32_t cells = (uint32_t)pw[0] + (np == 2 ? (uint32_t)pw[1] : 0u);
+  p.kappa_bytes = cells * SL::KB;
+  p.us_bytes = cells * (SL::UB + (a.src ? SL::KB : 0));
+  return p;
+}
+
+// Issue the copies of input row r into a slot, all completing on one mbarrier
+// (lane 0 posts the expected byte count; a complete_tx that lands before it is
+// allowed, the phase cannot finish before lane 0 arrives).  u and s are
+// skipped on a Dirichlet ghost row; kappa comes from the clamped row.
+// extra_bytes > 0 (tests only) expects bytes that never arrive.
+template <bool BF>
+__device__ __forceinline__ void issue_row(const StreamArgs& a, const CopyPlan& cp, int r, int lane,
+                                          unsigned char* slot, uint64_t* bar, uint32_t extra_bytes) {
+  const bool periodic = a.bc == BC_PERIODIC;
+  const bool rin = periodic || (r >= 0 && r < a.ny);
+  if (lane == 0) mbar_arrive_expect_tx(bar, cp.kappa_bytes + (rin ? cp.us_bytes : 0u) + extra_bytes);
+  if (cp.active && (rin || cp.field == 0)) {
+    const int rr = periodic ? wrap_index(r, a.ny) : clamp_index(r, a.ny);
+    const size_t g = (size_t)rr * a.nx + cp.col;
+    const size_t eb = cp.field == 1 ? Io<BF>::U_BYTES : Io<BF>::KS_BYTES;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    bulk_g2s(slot + cp.dst_off, cp.src_base + g * eb, cp.bytes, bar);
   }
 }
 
@@ -453,11 +511,15 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
   constexpr int OW = 128 - 2 * HALO;
   using SL = Slot<BF>;
   using IO = Io<BF>;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int R = a.stages;
+  // shared memory: [row rings of all warps][mbarriers][face rings of all warps]
   unsigned char* ring = smem + (size_t)wib * R * SL::BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)(blockDim.x >> 5) * R * SL::BYTES) + wib * R;
-  const int item = blockIdx.x * (blockDim.x >> 5) + wib;
+  unsigned char* bar_base = smem + (size_t)nwarps * R * SL::BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bar_base) + wib * R;
+  float4* face = reinterpret_cast<float4*>(bar_base + (size_t)nwarps * R * sizeof(uint64_t) +
+                                           (size_t)wib * face_ring_rows(K) * FACE_SLOT_BYTES);
+  const int item = blockIdx.x * nwarps + wib;
   const int nx = a.nx, ny = a.ny, d = FULL ? K : a.depth;
   const bool periodic = a.bc == BC_PERIODIC;
   const int strip = item % a.n_strips, chunk = item / a.n_strips;
@@ -472,25 +534,26 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
   // supplies kappa to a Dirichlet ghost lane.
   const int own = x0 - x0a + 4 * lane;
   const int kofs = lc.kb ? lc.xv - x0a : own;
+  const CopyPlan cp = make_copy_plan<BF>(a, x0a, lane);
 
   if (lane == 0) {
     for (int i = 0; i < R; ++i) mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int i = 0; i < R && i < nrows; ++i)
-      issue_row<BF>(a, r_first + i, x0a, ring + (size_t)i * SL::BYTES, &bars[i],
-                    (a.inject_on && r_first + i == a.inject_row) ? 16u : 0u);
   }
   __syncwarp();
+  for (int i = 0; i < R && i < nrows; ++i)
+    issue_row<BF>(a, cp, r_first + i, lane, ring + (size_t)i * SL::BYTES, &bars[i],
+                  (a.inject_on && r_first + i == a.inject_row) ? 16u : 0u);
 
   Pipe<K, BF> pipe;
-  pipe.init();
+  pipe.init(face, lane);
   int failed_at = -1;
-  for (int i = 0; i < nrows; ++i) {
+  auto body = [&](auto odd, int i) -> bool {
     const int r_in = r_first + i;
     const int slot = i & (R - 1);
     if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i / R) & 1u, a.wait_limit)) {
       failed_at = i;
-      break;
+      return false;
     }
     const unsigned char* srow = ring + (size_t)slot * SL::BYTES;
     const bool rin = periodic || (r_in >= 0 && r_in < ny);
@@ -504,17 +567,23 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
     }
     __syncwarp();
     // Every lane has read the slot: refill it with row r_in + R.
-    if (lane == 0 && i + R < nrows) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_row<BF>(a, r_in + R, x0a, ring + (size_t)slot * SL::BYTES, &bars[slot],
+    if (i + R < nrows)
+      issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
                     (a.inject_on && r_in + R == a.inject_row) ? 16u : 0u);
-    }
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
-    pipe.step(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn, sn, out, packed);
+    pipe.template step<decltype(odd)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn, sn,
+                                                   out, packed);
     const int ro = r_in - d;
     if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, true, out, packed);
+    return true;
+  };
+  int i = 0;
+  for (; i + 1 < nrows; i += 2) {  // unrolled by 2: level rows alternate roles
+    if (!body(Bool<false>{}, i)) break;
+    if (!body(Bool<true>{}, i + 1)) break;
   }
+  if (failed_at < 0 && i < nrows) body(Bool<false>{}, i);
   if (failed_at >= 0) {
     // Record the timeout, then give every row still in flight (issued but not
     // consumed) one more bounded wait so no copy targets this CTA's shared
@@ -542,8 +611,27 @@ __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
 // host launchers
 // ---------------------------------------------------------------------------
 namespace {
-// Per (storage, depth) kernel: devices on which the shared-memory opt-in was set.
-unsigned g_bulk_attr_done[2][9];
+// Per (variant, storage, depth) kernel: devices (bit per ordinal < 32) on which
+// the shared-memory opt-in was set.  Internal linkage: one per translation
+// unit and library (a function-local static of a template would be merged
+// across every shared object loaded in the process).
+unsigned g_smem_attr_done[2][2][9];
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory, once per device.
+inline cudaError_t ensure_smem_optin(const void* fn, unsigned& done, size_t shm) {
+  if (shm <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && (done & (1u << dev))) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (shm > (size_t)optin) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess && dev < 32) done |= 1u << dev;
+  return e;
+}
 }  // namespace
 
 template <int K, bool BF>
@@ -575,28 +663,17 @@ cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
   const int wpb = p.warps_per_block;
   const long long blocks = (items + wpb - 1) / wpb;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (p.variant == 1) {
-    const size_t shm = bulk_smem_bytes(BF, wpb, p.stages);
-    // Opt in to more than 48 KB of dynamic shared memory, once per device.
-    // The flag has internal linkage (one per translation unit and library):
-    // a function-local static of a template would be merged across every
-    // shared object loaded in the process.
-    unsigned& attr_done = g_bulk_attr_done[BF ? 1 : 0][K];  // bit per device ordinal (< 32)
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (shm > 48 * 1024 && (dev >= 32 || !(attr_done & (1u << dev)))) {
-      int optin = 0;
-      cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(stream_bulk_kernel<K, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               optin);
-      if (e != cudaSuccess) return e;
-      if (dev < 32) attr_done |= 1u << dev;
-    }
+  const size_t face = (size_t)wpb * face_ring_rows(K) * FACE_SLOT_BYTES;
+  const bool bulk = p.variant == 1;
+  const size_t shm = face + (bulk ? bulk_smem_bytes(BF, wpb, p.stages) : 0);
+  cudaError_t e = ensure_smem_optin(bulk ? (const void*)stream_bulk_kernel<K, BF>
+                                         : (const void*)stream_kernel<K, BF>,
+                                    g_smem_attr_done[bulk ? 1 : 0][BF ? 1 : 0][K], shm);
+  if (e != cudaSuccess) return e;
+  if (bulk)
     stream_bulk_kernel<K, BF><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
-  } else {
-    stream_kernel<K, BF><<<(unsigned)blocks, 32 * wpb, 0, s>>>(a);
-  }
+  else
+    stream_kernel<K, BF><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
   return cudaGetLastError();
 }
 
