@@ -71,6 +71,7 @@ cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u
                                 float* gk, int nx, int ny, float dt, int bc, cudaStream_t s) {
   dim3 block(ADJ_BX, ADJ_BY);
   dim3 grid((nx + ADJ_BX - 1) / ADJ_BX, (ny + ADJ_BY - 1) / ADJ_BY);
+  (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
   adjoint_step<<<grid, block, 0, s>>>(lam, lam_out, u, k, gk, nx, ny, dt, 0.5f * dt, bc);
   return cudaGetLastError();
 }

@@ -190,6 +190,7 @@ cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrid
   const size_t shm = batch_smem(threads);
   cudaError_t e = ensure_smem_optin((const void*)batch_kernel, g_batch_attr_done, shm);
   if (e != cudaSuccess) return e;
+  (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
   e = cudaMemsetAsync(work, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   batch_kernel<<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, work);

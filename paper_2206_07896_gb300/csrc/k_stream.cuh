@@ -627,8 +627,12 @@ inline cudaError_t ensure_smem_optin(const void* fn, unsigned& done, size_t shm)
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  if (shm > (size_t)optin) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
+  if (shm > (size_t)dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   if (e == cudaSuccess && dev < 32) done |= 1u << dev;
   return e;
 }
@@ -670,6 +674,7 @@ cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
                                          : (const void*)stream_kernel<K, BF>,
                                     g_smem_attr_done[bulk ? 1 : 0][BF ? 1 : 0][K], shm);
   if (e != cudaSuccess) return e;
+  (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
   if (bulk)
     stream_bulk_kernel<K, BF><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
   else

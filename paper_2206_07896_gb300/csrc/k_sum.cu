@@ -102,6 +102,7 @@ __global__ void bf16k_unpack_kernel(const uint32_t* __restrict__ st, float* __re
 }
 
 int elementwise_blocks(long long n) {
+  (void)cudaGetLastError();  // called right before each launch: drop a stale non-sticky error
   long long b = (n + 255) / 256;
   return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
@@ -115,6 +116,7 @@ int heat_sum_blocks(long long n) {
 
 cudaError_t launch_heat_sum(const void* u, long long n, int dtype, double* d_out, double* partials,
                             int nblocks, cudaStream_t s) {
+  (void)cudaGetLastError();  // drop a stale non-sticky error so the checks below are these launches'
   if (dtype == CPB_F32) {
     const float* f = static_cast<const float*>(u);
     long long mis = (long long)(reinterpret_cast<uintptr_t>(f) & 15) / 4;

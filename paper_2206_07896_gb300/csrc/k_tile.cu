@@ -61,6 +61,7 @@ __global__ void tile_step_f32(const float* __restrict__ u, float* __restrict__ u
 cudaError_t launch_tile_f32(const float* u_in, float* u_out, const float* kappa, const float* src,
                             int nx, int ny, float dt, int bc, dim3 grid, dim3 block, size_t shm,
                             cudaStream_t s) {
+  (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
   tile_step_f32<<<grid, block, shm, s>>>(u_in, u_out, kappa, src, nx, ny, dt, 0.5f * dt, bc);
   return cudaGetLastError();
 }
