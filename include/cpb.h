@@ -161,6 +161,25 @@ size_t cpb_heat_sum_workspace_bytes(int nx, int ny);
 cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
                         void* workspace, size_t ws_bytes, cpb_stream_t stream);
 
+/* cpb_heat_sum without a workspace: the same FP64 heat sum, for callers that
+ * cannot allocate device memory — code that runs where cudaMalloc is not
+ * available to it (a host framework that owns all device memory through its
+ * own pool, an embedding that forbids new allocations after start-up) or
+ * where the implicit device synchronisation of cudaMalloc/cudaFree is not
+ * acceptable (latency-critical loops).  There is no counterpart in the paper.
+ *
+ * The per-block partial sums live in a 32 KB array inside the library (one
+ * per GPU that loads it, held until the process exits).  Grids of more than
+ * 2^26 cells (67,108,864) are rejected with CPB_ERR_WORKSPACE before any
+ * launch; use cpb_heat_sum for those.  The call allocates nothing.  Its
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls whose executions overlap on the
+ * GPU (unordered streams) race and may return wrong sums.  The blocking
+ * differs from cpb_heat_sum, so the two may differ in the last bits. */
+cpb_status cpb_heat_sum_noalloc(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
+                                cpb_stream_t stream);
+
 /* BF16 conversions on the device (round to nearest even).
  * cpb_bf16_round: out[i] = rn_bf16(x[i]) (bf16 bit patterns).
  * cpb_bf16k_pack: state[i] = hi | cmp << 16 with hi = rn(u), cmp = rn(hi - u).

@@ -87,6 +87,7 @@ _SIGS = {
     "cpb_debug_set": (_i, [_i, _i]),
     "cpb_heat_sum_workspace_bytes": (_sz, [_i, _i]),
     "cpb_heat_sum": (_i, [_vp, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "cpb_heat_sum_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "cpb_bf16_round": (_i, [_vp, _vp, _ll, _vp]),
     "cpb_bf16k_pack": (_i, [_vp, _vp, _ll, _vp]),
     "cpb_bf16k_unpack": (_i, [_vp, _vp, _ll, _vp]),
@@ -222,6 +223,9 @@ class Library:
     def cpb_heat_sum(self, u, nx, ny, dtype, d_out, workspace, ws_bytes, stream=None):
         self._call("cpb_heat_sum", ptr(u), nx, ny, dtype, ptr(d_out), ptr(workspace), ws_bytes,
                    stream_handle(stream))
+
+    def cpb_heat_sum_noalloc(self, u, nx, ny, dtype, d_out, stream=None):
+        self._call("cpb_heat_sum_noalloc", ptr(u), nx, ny, dtype, ptr(d_out), stream_handle(stream))
 
     def cpb_bf16_round(self, x, out, n, stream=None):
         self._call("cpb_bf16_round", ptr(x), ptr(out), n, stream_handle(stream))

@@ -420,6 +420,21 @@ cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* 
                                    reinterpret_cast<cudaStream_t>(stream)));
 }
 
+cpb_status cpb_heat_sum_noalloc(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
+                                cpb_stream_t stream) {
+  if (!u || !d_out || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  if (!aligned(u, 4) || !aligned(d_out, 8)) return CPB_ERR_INVALID_VALUE;
+  const long long n = (long long)nx * ny;
+  if (n > heat_sum_noalloc_max_cells()) {
+    g_last_error = "grid larger than the built-in heat-sum scratch allows (" +
+                   std::to_string(heat_sum_noalloc_max_cells()) + " cells); use cpb_heat_sum";
+    return CPB_ERR_WORKSPACE;
+  }
+  return from_cuda(launch_heat_sum_noalloc(u, n, (int)dtype, d_out,
+                                           reinterpret_cast<cudaStream_t>(stream)));
+}
+
 cpb_status cpb_bf16_round(const float* x, uint16_t* out, long long n, cpb_stream_t stream) {
   if (n < 0 || (n > 0 && (!x || !out))) return CPB_ERR_INVALID_VALUE;
   if (n == 0) return CPB_SUCCESS;

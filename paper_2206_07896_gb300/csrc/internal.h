@@ -84,3 +84,10 @@ namespace cpb {
 cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u, const float* k,
                                 float* gk, int nx, int ny, float dt, int bc, cudaStream_t s);
 }  // namespace cpb
+
+namespace cpb {
+// Heat sum with partials in a file-scope device array (k_sum.cu).
+long long heat_sum_noalloc_max_cells();
+cudaError_t launch_heat_sum_noalloc(const void* u, long long n, int dtype, double* d_out,
+                                    cudaStream_t s);
+}  // namespace cpb

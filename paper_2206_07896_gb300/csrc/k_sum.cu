@@ -6,6 +6,8 @@
 // tree, block tree, then one block over the per-block partials), so the same
 // input gives the same bits on the same device.  This is the only FP64
 // arithmetic on the GPU path.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -145,6 +147,60 @@ cudaError_t launch_bf16k_pack(const float* u, uint32_t* st, long long n, cudaStr
 cudaError_t launch_bf16k_unpack(const uint32_t* st, float* u, long long n, cudaStream_t s) {
   bf16k_unpack_kernel<<<elementwise_blocks(n), 256, 0, s>>>(st, u, n);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Heat sum that allocates nothing (cpb_heat_sum_noalloc)
+// ---------------------------------------------------------------------------
+// For callers that cannot allocate device memory: the per-block partial sums
+// of the two-pass reduction live in a file-scope device array instead of a
+// caller workspace.  Every GPU that loads the library holds this array (32 KB)
+// until the process exits.  One partial per block of NOALLOC_CELLS_PER_BLOCK
+// cells, so grids of up to NOALLOC_MAX_PARTIALS * NOALLOC_CELLS_PER_BLOCK
+// = 2^26 cells are accepted; larger grids are rejected before any launch.
+// All calls share the array and it keeps the previous call's contents; every
+// partial that is read is first written by the same call, so nothing needs
+// clearing.  Calls whose executions overlap on the GPU (different streams,
+// no ordering between them) race on the array.
+namespace {
+constexpr int NOALLOC_MAX_PARTIALS = 4096;
+constexpr long long NOALLOC_CELLS_PER_BLOCK = 16384;
+}  // namespace
+
+static __device__ __align__(256) double g_heat_sum_scratch[NOALLOC_MAX_PARTIALS];
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[64];  // device address of g_heat_sum_scratch, per device ordinal
+
+// Set-up, once per device, with that device current: the host-side name of a
+// __device__ array is not a device address, so ask the runtime for it.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_heat_sum_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+long long heat_sum_noalloc_max_cells() { return NOALLOC_MAX_PARTIALS * NOALLOC_CELLS_PER_BLOCK; }
+
+cudaError_t launch_heat_sum_noalloc(const void* u, long long n, int dtype, double* d_out,
+                                    cudaStream_t s) {
+  double* partials = nullptr;
+  cudaError_t e = noalloc_scratch(&partials);
+  if (e != cudaSuccess) return e;
+  const int nblocks = (int)((n + NOALLOC_CELLS_PER_BLOCK - 1) / NOALLOC_CELLS_PER_BLOCK);
+  return launch_heat_sum(u, n, dtype, d_out, partials, nblocks, s);
 }
 
 }  // namespace cpb
