@@ -107,7 +107,8 @@ def test_batched_invalid_device_descriptor_is_reported(dev):
     grids = small_batch(5, W.PERIODIC)[:10]
     u, k, s, off = pack(grids, dev)
     uo = torch.full_like(u, -1.0)
-    descs = cpb.batch_descriptors(u.clone(), uo, k, s, off, [g.nx for g in grids],
+    uin = u.clone()                   # keep a reference: the descriptors hold raw pointers
+    descs = cpb.batch_descriptors(uin, uo, k, s, off, [g.nx for g in grids],
                                   [g.ny for g in grids], [g.steps for g in grids],
                                   [g.dt for g in grids])
     order, n_large = L.cpb_batch_order(descs, None)
