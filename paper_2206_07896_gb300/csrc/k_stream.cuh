@@ -4,9 +4,11 @@
 //   A warp owns a strip of 128 columns (4 consecutive columns per lane, so a
 //   row of the strip is one 128-bit access per lane) and a chunk of output
 //   rows [y0, y1).  It streams rows y0-d .. y1+d-1 of u, kappa and s from HBM
-//   once and advances them d <= K time steps in registers: level t (1..d)
-//   produces row r_in - t from level t-1's rows r_in-t-1 .. r_in-t+1 as soon as
-//   input row r_in has arrived.  Level t is valid on columns [x0+t, x0+128-t),
+//   once and advances them d <= K time steps in registers, as a skewed
+//   wavefront: when input row r_in arrives, level t (1..d) produces row
+//   r_in - 2t + 1 from level t-1 rows finished in earlier iterations, so the
+//   levels of one iteration are independent (see Pipe).  Level t is valid on
+//   columns [x0+t, x0+128-t),
 //   so the strip writes its inner 128 - 2*HALO columns (HALO = K rounded up to
 //   a multiple of 4, which keeps stores 16-byte aligned); neighbouring strips
 //   overlap by 2*HALO columns.  West/east neighbours of a lane's first/last
@@ -132,9 +134,9 @@ struct Io<true> {
 
 __device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
 
-template <bool B>
-struct Bool {
-  static constexpr bool value = B;
+template <int V>
+struct Int {
+  static constexpr int value = V;
 };
 
 // Column geometry of one lane's 4 cells inside its strip.
@@ -176,58 +178,71 @@ __device__ __forceinline__ LaneCols lane_cols(int xs, int nx, bool periodic) {
 constexpr int FACE_FE = 0, FACE_FN = 1, FACE_DS = 2;
 constexpr int FACE_SLOT_BYTES = 3 * 32 * 16;
 
-__host__ __device__ constexpr int face_ring_rows(int k) { return k + 2; }
+// Rows the face ring must hold for depth k: level k reads faceN of row
+// r_in - 2k, the newest row written is r_in.
+__host__ __device__ constexpr int face_ring_rows(int k) { return 2 * k + 1; }
 
-// The K-level pipeline of one warp strip.  At the start of the iteration that
-// receives input row r_in, for level t = 0..K-1 the two rows r_in-t-2 and
-// r_in-t-1 are held in W[t][0..1] with roles that alternate between even and
-// odd iterations (ODD), so advancing the window needs no register copies.
-// The ring holds faceE / dt*s of rows >= r_in-K and faceN of rows >= r_in-K-1.
+// The K-level pipeline of one warp strip, as a skewed wavefront.
+//
+// Iteration i (input row r_in = r_first + i) lets level t (1..K) produce row
+// r_in - 2t + 1.  Its three input rows from level t-1 were all finished in
+// earlier iterations (level t-1 produced them at iterations i-3, i-2, i-1;
+// level 0 is the input, read at i-2, i-1, i), so the K levels of one
+// iteration are independent of each other.  Each level keeps its last three
+// outputs in W[t][slot] with slot = iteration mod 3; levels are evaluated
+// from the top down, so level t+1 reads level t's oldest row before level t
+// overwrites it, and with the iteration loop unrolled by 3 every slot index
+// is a compile-time constant (no register copies).
 template <int K, bool BF>
 struct Pipe {
-  float4 W[K][2];
+  float4 W[K][3];  // W[0]: input rows; W[t]: outputs of level t
   float4 kprev;
-  float4* ring;  // this lane's slice: ring[(slot * 3 + field) * 32]
-  int rf, slot_in;
+  float4* ring;    // this lane's slice: ring[(slot * 3 + field) * 32]
+  int slot_in;     // face-ring slot of the current input row
+
+  static constexpr int RF = face_ring_rows(K);
 
   __device__ __forceinline__ void init(float4* warp_ring, int lane) {
 #pragma unroll
-    for (int t = 0; t < K; ++t) W[t][0] = W[t][1] = f4(0.0f);
+    for (int t = 0; t < K; ++t) W[t][0] = W[t][1] = W[t][2] = f4(0.0f);
     kprev = f4(0.0f);
     ring = warp_ring + lane;
-    rf = face_ring_rows(K);
     slot_in = 0;
-    for (int i = 0; i < 3 * rf; ++i) ring[i * 32] = f4(0.0f);
+    for (int i = 0; i < 3 * RF; ++i) ring[i * 32] = f4(0.0f);
   }
 
   __device__ __forceinline__ float4& at(int slot, int field) { return ring[(slot * 3 + field) * 32]; }
-  __device__ __forceinline__ int back(int t) const {
-    int sl = slot_in - t;
-    return sl < 0 ? sl + rf : sl;
+  __device__ __forceinline__ int back(int n) const {
+    int sl = slot_in - n;
+    return sl < 0 ? sl + RF : sl;
   }
 
-  // Consume input row r_in; leaves level d's row r_in - d in `out` (and, for
-  // BF16-Kahan storage, its packed words in `packed`).  FULL: d == K.
-  template <bool ODD, bool FULL>
+  // Consume input row r_in at iteration phase P (= iteration index mod 3).
+  // Leaves the row r_in - 2d + 1 of level d in `out` (and, for BF16-Kahan
+  // storage, its packed words in `packed`).  FULL: d == K.
+  template <int P, bool FULL>
   __device__ __forceinline__ void step(int r_in, int d, int ny, bool periodic, const LaneCols& lc,
                                        float dt, float hdt, float4 un, float4 kn, float4 sn,
                                        float4& out, uint4& packed) {
-    constexpr int S_ = ODD ? 1 : 0, C_ = ODD ? 0 : 1;
-    const float4 fn_new = make_float4(kprev.x + kn.x, kprev.y + kn.y, kprev.z + kn.z, kprev.w + kn.w);
+    constexpr int P1 = (P + 1) % 3, P2 = (P + 2) % 3;
     const float kx_e = __shfl_down_sync(CPB_FULL, kn.x, 1);
     at(slot_in, FACE_FE) = make_float4(kn.x + kn.y, kn.y + kn.z, kn.z + kn.w, kn.w + kx_e);
     at(slot_in, FACE_DS) = make_float4(dt * sn.x, dt * sn.y, dt * sn.z, dt * sn.w);
-    at(back(1), FACE_FN) = fn_new;
+    at(back(1), FACE_FN) = make_float4(kprev.x + kn.x, kprev.y + kn.y, kprev.z + kn.z, kprev.w + kn.w);
+    kprev = kn;
+    W[0][P] = un;  // input row r_in replaces r_in - 3
 
-    float4 nw = un;  // the row level t-1 produced in this iteration
 #pragma unroll
-    for (int t = 1; t <= K; ++t) {
+    for (int t = K; t >= 1; --t) {
       if (FULL || t <= d) {
-        const int rho = r_in - t;
-        const int sl = back(t), sls = back(t + 1);
-        const float4 C = W[t - 1][C_], S = W[t - 1][S_], N = nw;
-        const float4 fe = at(sl, FACE_FE), ds = at(sl, FACE_DS), fs = at(sls, FACE_FN);
-        const float4 fn = (t == 1) ? fn_new : at(sl, FACE_FN);
+        const int rho = r_in - 2 * t + 1;
+        // level t-1 rows rho-1, rho, rho+1
+        const float4 S = (t == 1) ? W[0][P1] : W[t - 1][P];
+        const float4 C = (t == 1) ? W[0][P2] : W[t - 1][P1];
+        const float4 N = (t == 1) ? W[0][P] : W[t - 1][P2];
+        const int sl = back(2 * t - 1), sls = back(2 * t);
+        const float4 fe = at(sl, FACE_FE), ds = at(sl, FACE_DS);
+        const float4 fn = at(sl, FACE_FN), fs = at(sls, FACE_FN);
         const float uWx = __shfl_up_sync(CPB_FULL, C.w, 1);
         const float uEw = __shfl_down_sync(CPB_FULL, C.x, 1);
         const float fWx = __shfl_up_sync(CPB_FULL, fe.w, 1);
@@ -236,10 +251,11 @@ struct Pipe {
         v.y = cell_update(C.y, C.x, C.z, S.y, N.y, fe.x, fe.y, fs.y, fn.y, ds.y, hdt);
         v.z = cell_update(C.z, C.y, C.w, S.z, N.z, fe.y, fe.z, fs.z, fn.z, ds.z, hdt);
         v.w = cell_update(C.w, C.z, uEw, S.w, N.w, fe.z, fe.w, fs.w, fn.w, ds.w, hdt);
+        uint4 pk = make_uint4(0, 0, 0, 0);
         if (BF) {
           float e0, e1, e2, e3;
-          packed = make_uint4(kahan_round(v.x, e0), kahan_round(v.y, e1), kahan_round(v.z, e2),
-                              kahan_round(v.w, e3));
+          pk = make_uint4(kahan_round(v.x, e0), kahan_round(v.y, e1), kahan_round(v.z, e2),
+                          kahan_round(v.w, e3));
           v = make_float4(e0, e1, e2, e3);
         }
         if (!periodic) {  // Dirichlet ghosts stay at zero
@@ -249,15 +265,22 @@ struct Pipe {
           v.z = lc.ine[2] ? v.z : 0.0f;
           v.w = lc.ine[3] ? v.w : 0.0f;
         }
-        W[t - 1][S_] = nw;  // becomes the centre row; the old centre becomes south
-        nw = v;
+        if (FULL ? (t == K) : (t == d)) {
+          out = v;
+          packed = pk;
+        }
+        if (t < K) W[t][P] = v;  // replaces this level's output of iteration i-3
       }
     }
-    out = nw;
-    kprev = kn;
-    slot_in = (slot_in + 1 == rf) ? 0 : slot_in + 1;
+    slot_in = (slot_in + 1 == RF) ? 0 : slot_in + 1;
   }
 };
+
+// Iteration counts of a strip chunk [y0, y1) at depth d: input rows
+// y0-d .. y1+d-1 are read (n_in iterations); the skew needs d-1 more
+// iterations to drain (the last output row y1-1 leaves level d at input
+// index n_in + d - 2).
+__device__ __forceinline__ int skew_iterations(int rows, int d) { return rows + 3 * d - 1; }
 
 // Store one output row of a lane (only columns this strip owns).
 template <bool BF>
@@ -341,25 +364,31 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
 
   Pipe<K, BF> pipe;
   pipe.init(face_ring, lane);
-  const int r_end = y1 + d;
+  const int r_first = y0 - d;
+  const int n_in = (y1 - y0) + 2 * d;             // input rows
+  const int n_it = skew_iterations(y1 - y0, d);   // iterations including the drain
   float4 pu, pk, ps;
-  load_row(y0 - d, pu, pk, ps);
-  auto body = [&](auto odd, int r_in) {
-    const float4 un = pu, kn = pk, sn = ps;
-    if (r_in + 1 < r_end) load_row(r_in + 1, pu, pk, ps);
+  load_row(r_first, pu, pk, ps);
+  auto body = [&](auto phase, int i) {
+    const int r_in = r_first + i;
+    float4 un = pu, kn = pk, sn = ps;
+    if (i + 1 < n_in) load_row(r_in + 1, pu, pk, ps);
+    if (i >= n_in) un = kn = sn = f4(0.0f);  // drain: outputs that depend on these are not stored
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
-    pipe.template step<decltype(odd)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn, sn,
-                                                   out, packed);
-    const int ro = r_in - d;
+    pipe.template step<decltype(phase)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
+                                                     sn, out, packed);
+    const int ro = r_in - 2 * d + 1;
     if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, a.vec, out, packed);
   };
-  int r_in = y0 - d;
-  for (; r_in + 1 < r_end; r_in += 2) {  // unrolled by 2: level rows alternate roles
-    body(Bool<false>{}, r_in);
-    body(Bool<true>{}, r_in + 1);
+  int i = 0;
+  for (; i + 2 < n_it; i += 3) {  // unrolled by 3: window slots are compile-time constants
+    body(Int<0>{}, i);
+    body(Int<1>{}, i + 1);
+    body(Int<2>{}, i + 2);
   }
-  if (r_in < r_end) body(Bool<false>{}, r_in);
+  if (i < n_it) body(Int<0>{}, i);
+  if (i + 1 < n_it) body(Int<1>{}, i + 1);
 }
 
 template <int K, bool BF>
@@ -547,43 +576,48 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
 
   Pipe<K, BF> pipe;
   pipe.init(face, lane);
+  const int n_it = skew_iterations(y1 - y0, d);  // nrows input iterations + the drain
   int failed_at = -1;
-  auto body = [&](auto odd, int i) -> bool {
+  auto body = [&](auto phase, int i) -> bool {
     const int r_in = r_first + i;
-    const int slot = i & (R - 1);
-    if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i / R) & 1u, a.wait_limit)) {
-      failed_at = i;
-      return false;
+    float4 kn = f4(0.0f), un = f4(0.0f), sn = f4(0.0f);
+    if (i < nrows) {
+      const int slot = i & (R - 1);
+      if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i / R) & 1u, a.wait_limit)) {
+        failed_at = i;
+        return false;
+      }
+      const unsigned char* srow = ring + (size_t)slot * SL::BYTES;
+      const bool rin = periodic || (r_in >= 0 && r_in < ny);
+      kn = IO::sk4(srow + SL::K_OFF, kofs);
+      if (lc.kb == 1) kn = f4(kn.x);
+      if (lc.kb == 2) kn = f4(kn.w);
+      if (rin && lc.cin4) {
+        un = IO::su4(srow, own);
+        if (a.src) sn = IO::sk4(srow + SL::S_OFF, own);
+      }
+      __syncwarp();
+      // Every lane has read the slot: refill it with row r_in + R.
+      if (i + R < nrows)
+        issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
+                      (a.inject_on && r_in + R == a.inject_row) ? 16u : 0u);
     }
-    const unsigned char* srow = ring + (size_t)slot * SL::BYTES;
-    const bool rin = periodic || (r_in >= 0 && r_in < ny);
-    float4 kn = IO::sk4(srow + SL::K_OFF, kofs);
-    if (lc.kb == 1) kn = f4(kn.x);
-    if (lc.kb == 2) kn = f4(kn.w);
-    float4 un = f4(0.0f), sn = f4(0.0f);
-    if (rin && lc.cin4) {
-      un = IO::su4(srow, own);
-      if (a.src) sn = IO::sk4(srow + SL::S_OFF, own);
-    }
-    __syncwarp();
-    // Every lane has read the slot: refill it with row r_in + R.
-    if (i + R < nrows)
-      issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
-                    (a.inject_on && r_in + R == a.inject_row) ? 16u : 0u);
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
-    pipe.template step<decltype(odd)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn, sn,
-                                                   out, packed);
-    const int ro = r_in - d;
+    pipe.template step<decltype(phase)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
+                                                     sn, out, packed);
+    const int ro = r_in - 2 * d + 1;
     if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, true, out, packed);
     return true;
   };
   int i = 0;
-  for (; i + 1 < nrows; i += 2) {  // unrolled by 2: level rows alternate roles
-    if (!body(Bool<false>{}, i)) break;
-    if (!body(Bool<true>{}, i + 1)) break;
+  for (; i + 2 < n_it; i += 3) {  // unrolled by 3: window slots are compile-time constants
+    if (!body(Int<0>{}, i)) break;
+    if (!body(Int<1>{}, i + 1)) break;
+    if (!body(Int<2>{}, i + 2)) break;
   }
-  if (failed_at < 0 && i < nrows) body(Bool<false>{}, i);
+  if (failed_at < 0 && i < n_it) body(Int<0>{}, i);
+  if (failed_at < 0 && i + 1 < n_it) body(Int<1>{}, i + 1);
   if (failed_at >= 0) {
     // Record the timeout, then give every row still in flight (issued but not
     // consumed) one more bounded wait so no copy targets this CTA's shared
