@@ -22,7 +22,7 @@ OUT = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "--expt-relaxed-constexpr"]
-VARIANTS = {"libcpb.so": ["--fmad=true"], "libcpb_nofma.so": ["--fmad=false"]}
+VARIANTS = {"libcpb.so": ["--fmad=true"], "libcpb_nofma.so": ["--fmad=false", "-DCPB_EXACT_ARITH"]}
 
 
 def nvcc() -> str:

@@ -4,11 +4,10 @@
 //   A warp owns a strip of 128 columns (4 consecutive columns per lane, so a
 //   row of the strip is one 128-bit access per lane) and a chunk of output
 //   rows [y0, y1).  It streams rows y0-d .. y1+d-1 of u, kappa and s from HBM
-//   once and advances them d <= K time steps in registers, as a skewed
-//   wavefront: when input row r_in arrives, level t (1..d) produces row
-//   r_in - 2t + 1 from level t-1 rows finished in earlier iterations, so the
-//   levels of one iteration are independent (see Pipe).  Level t is valid on
-//   columns [x0+t, x0+128-t),
+//   once and advances them d <= K time steps in registers: level t (1..d)
+//   produces row r_in - t from level t-1's rows r_in-t-1 .. r_in-t+1 as soon as
+//   input row r_in has arrived (see Pipe for the flux form of the update).
+//   Level t is valid on columns [x0+t, x0+128-t),
 //   so the strip writes its inner 128 - 2*HALO columns (HALO = K rounded up to
 //   a multiple of 4, which keeps stores 16-byte aligned); neighbouring strips
 //   overlap by 2*HALO columns.  West/east neighbours of a lane's first/last
@@ -178,33 +177,64 @@ __device__ __forceinline__ LaneCols lane_cols(int xs, int nx, bool periodic) {
 constexpr int FACE_FE = 0, FACE_FN = 1, FACE_DS = 2;
 constexpr int FACE_SLOT_BYTES = 3 * 32 * 16;
 
-// Rows the face ring must hold for depth k: level k reads faceN of row
-// r_in - 2k, the newest row written is r_in.
-__host__ __device__ constexpr int face_ring_rows(int k) { return 2 * k + 1; }
+// Rows the face ring must hold for depth k: level k reads row r_in - k, the
+// newest row written is r_in.
+__host__ __device__ constexpr int face_ring_rows(int k) { return k + 1; }
 
-// The K-level pipeline of one warp strip, as a skewed wavefront.
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// Packed FP32 pair arithmetic (sm_100+): each component is rounded exactly as
+// the scalar operation.  b - a is formed as fma(a, -1, b), which is exact in
+// the product and rounds once, i.e. the same bits as the subtraction.
+__device__ __forceinline__ float2 sub2(float2 b, float2 a) {
+  return __ffma2_rn(a, make_float2(-1.0f, -1.0f), b);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// h * acc + ds: fused in the default build; two roundings (product, then
+// sum) in the build that reproduces the canonical order bit for bit.
+__device__ __forceinline__ float2 madd2(float2 h, float2 acc, float2 ds) {
+#ifdef CPB_EXACT_ARITH
+  return __fadd2_rn(__fmul2_rn(h, acc), ds);
+#else
+  return __ffma2_rn(h, acc, ds);
+#endif
+}
+
+// The K-level pipeline of one warp strip, in flux form.
 //
-// Iteration i (input row r_in = r_first + i) lets level t (1..K) produce row
-// r_in - 2t + 1.  Its three input rows from level t-1 were all finished in
-// earlier iterations (level t-1 produced them at iterations i-3, i-2, i-1;
-// level 0 is the input, read at i-2, i-1, i), so the K levels of one
-// iteration are independent of each other.  Each level keeps its last three
-// outputs in W[t][slot] with slot = iteration mod 3; levels are evaluated
-// from the top down, so level t+1 reads level t's oldest row before level t
-// overwrites it, and with the iteration loop unrolled by 3 every slot index
-// is a compile-time constant (no register copies).
+// Iteration r_in (input row r_in) lets level t (1..K) produce row
+// rho = r_in - t from level t-1's rows rho (C, finished last iteration) and
+// rho+1 (N, finished this iteration by level t-1).  The update is evaluated
+// through face fluxes: F = (kc + kE)(uE - c) on each east face and
+// G = (kc + kN)(uN - c) on each north face.  The west term of a cell is
+// exactly -F of its west neighbour and the south term exactly -G of the row
+// below at the same level (negation and the commuted sums are exact), so
+//   acc = (fW + fE) + (fS + fN) = (F_i - F_{i-1}) + (G - G_below)
+// gives the canonical rounding sequence bit for bit while each flux is formed
+// once.  F_{i-1} of a lane's first cell comes from the lane to the west
+// (shuffle); G_below is this level's G of the previous iteration, carried in
+// registers.  The row-wise work (vertical fluxes and the combination) runs on
+// packed FP32 pairs.
+//
+// Registers: U[t][p] holds level t's row written at iteration parity p (t = 0
+// is the input), G[t][p] level t+1's north fluxes; with the row loop unrolled
+// by 2 every index is a compile-time constant and no copies are needed.
 template <int K, bool BF>
 struct Pipe {
-  float4 W[K][3];  // W[0]: input rows; W[t]: outputs of level t
+  float4 U[K][2];
+  float4 G[K][2];
   float4 kprev;
-  float4* ring;    // this lane's slice: ring[(slot * 3 + field) * 32]
-  int slot_in;     // face-ring slot of the current input row
+  float4* ring;  // this lane's slice: ring[(slot * 3 + field) * 32]
+  int slot_in;   // face-ring slot of the current input row
 
   static constexpr int RF = face_ring_rows(K);
 
   __device__ __forceinline__ void init(float4* warp_ring, int lane) {
 #pragma unroll
-    for (int t = 0; t < K; ++t) W[t][0] = W[t][1] = W[t][2] = f4(0.0f);
+    for (int t = 0; t < K; ++t) U[t][0] = U[t][1] = G[t][0] = G[t][1] = f4(0.0f);
     kprev = f4(0.0f);
     ring = warp_ring + lane;
     slot_in = 0;
@@ -217,40 +247,48 @@ struct Pipe {
     return sl < 0 ? sl + RF : sl;
   }
 
-  // Consume input row r_in at iteration phase P (= iteration index mod 3).
-  // Leaves the row r_in - 2d + 1 of level d in `out` (and, for BF16-Kahan
-  // storage, its packed words in `packed`).  FULL: d == K.
+  // Consume input row r_in at iteration parity P.  Leaves level d's row
+  // r_in - d in `out` (and, for BF16-Kahan storage, its packed words in
+  // `packed`).  FULL: d == K.
   template <int P, bool FULL>
   __device__ __forceinline__ void step(int r_in, int d, int ny, bool periodic, const LaneCols& lc,
                                        float dt, float hdt, float4 un, float4 kn, float4 sn,
                                        float4& out, uint4& packed) {
-    constexpr int P1 = (P + 1) % 3, P2 = (P + 2) % 3;
+    constexpr int Q = 1 - P;
     const float kx_e = __shfl_down_sync(CPB_FULL, kn.x, 1);
     at(slot_in, FACE_FE) = make_float4(kn.x + kn.y, kn.y + kn.z, kn.z + kn.w, kn.w + kx_e);
     at(slot_in, FACE_DS) = make_float4(dt * sn.x, dt * sn.y, dt * sn.z, dt * sn.w);
     at(back(1), FACE_FN) = make_float4(kprev.x + kn.x, kprev.y + kn.y, kprev.z + kn.z, kprev.w + kn.w);
     kprev = kn;
-    W[0][P] = un;  // input row r_in replaces r_in - 3
+    U[0][P] = un;
+    const float2 h2 = make_float2(hdt, hdt);
 
+    float4 nw = un;
 #pragma unroll
-    for (int t = K; t >= 1; --t) {
+    for (int t = 1; t <= K; ++t) {
       if (FULL || t <= d) {
-        const int rho = r_in - 2 * t + 1;
-        // level t-1 rows rho-1, rho, rho+1
-        const float4 S = (t == 1) ? W[0][P1] : W[t - 1][P];
-        const float4 C = (t == 1) ? W[0][P2] : W[t - 1][P1];
-        const float4 N = (t == 1) ? W[0][P] : W[t - 1][P2];
-        const int sl = back(2 * t - 1), sls = back(2 * t);
-        const float4 fe = at(sl, FACE_FE), ds = at(sl, FACE_DS);
-        const float4 fn = at(sl, FACE_FN), fs = at(sls, FACE_FN);
-        const float uWx = __shfl_up_sync(CPB_FULL, C.w, 1);
+        const int rho = r_in - t;
+        const float4 C = U[t - 1][Q], N = U[t - 1][P];
+        const int sl = back(t);
+        const float4 fe = at(sl, FACE_FE), fn = at(sl, FACE_FN), ds = at(sl, FACE_DS);
+        // east-face fluxes of the lane's 4 cells; the west flux of the first
+        // cell is the east flux of the lane to the west
         const float uEw = __shfl_down_sync(CPB_FULL, C.x, 1);
-        const float fWx = __shfl_up_sync(CPB_FULL, fe.w, 1);
-        float4 v;
-        v.x = cell_update(C.x, uWx, C.y, S.x, N.x, fWx, fe.x, fs.x, fn.x, ds.x, hdt);
-        v.y = cell_update(C.y, C.x, C.z, S.y, N.y, fe.x, fe.y, fs.y, fn.y, ds.y, hdt);
-        v.z = cell_update(C.z, C.y, C.w, S.z, N.z, fe.y, fe.z, fs.z, fn.z, ds.z, hdt);
-        v.w = cell_update(C.w, C.z, uEw, S.w, N.w, fe.z, fe.w, fs.w, fn.w, ds.w, hdt);
+        float4 F;
+        F.x = fe.x * (C.y - C.x);
+        F.y = fe.y * (C.z - C.y);
+        F.z = fe.z * (C.w - C.z);
+        F.w = fe.w * (uEw - C.w);
+        const float Fm1 = __shfl_up_sync(CPB_FULL, F.w, 1);
+        const float4 hsum = make_float4(F.x - Fm1, F.y - F.x, F.z - F.y, F.w - F.z);  // fW + fE
+        // north-face fluxes and the combination, on packed pairs
+        const float2 gl = mul2(lo2(fn), sub2(lo2(N), lo2(C)));
+        const float2 gh = mul2(hi2(fn), sub2(hi2(N), hi2(C)));
+        G[t - 1][P] = cat4(gl, gh);
+        const float4 Gb = G[t - 1][Q];  // north fluxes of row rho-1: minus the south terms
+        const float2 accl = add2(lo2(hsum), sub2(gl, lo2(Gb)));
+        const float2 acch = add2(hi2(hsum), sub2(gh, hi2(Gb)));
+        float4 v = cat4(add2(lo2(C), madd2(h2, accl, lo2(ds))), add2(hi2(C), madd2(h2, acch, hi2(ds))));
         uint4 pk = make_uint4(0, 0, 0, 0);
         if (BF) {
           float e0, e1, e2, e3;
@@ -265,22 +303,15 @@ struct Pipe {
           v.z = lc.ine[2] ? v.z : 0.0f;
           v.w = lc.ine[3] ? v.w : 0.0f;
         }
-        if (FULL ? (t == K) : (t == d)) {
-          out = v;
-          packed = pk;
-        }
-        if (t < K) W[t][P] = v;  // replaces this level's output of iteration i-3
+        if (t < K) U[t][P] = v;
+        nw = v;
+        packed = pk;
       }
     }
+    out = nw;
     slot_in = (slot_in + 1 == RF) ? 0 : slot_in + 1;
   }
 };
-
-// Iteration counts of a strip chunk [y0, y1) at depth d: input rows
-// y0-d .. y1+d-1 are read (n_in iterations); the skew needs d-1 more
-// iterations to drain (the last output row y1-1 leaves level d at input
-// index n_in + d - 2).
-__device__ __forceinline__ int skew_iterations(int rows, int d) { return rows + 3 * d - 1; }
 
 // Store one output row of a lane (only columns this strip owns).
 template <bool BF>
@@ -364,31 +395,25 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
 
   Pipe<K, BF> pipe;
   pipe.init(face_ring, lane);
-  const int r_first = y0 - d;
-  const int n_in = (y1 - y0) + 2 * d;             // input rows
-  const int n_it = skew_iterations(y1 - y0, d);   // iterations including the drain
+  const int r_end = y1 + d;
   float4 pu, pk, ps;
-  load_row(r_first, pu, pk, ps);
-  auto body = [&](auto phase, int i) {
-    const int r_in = r_first + i;
-    float4 un = pu, kn = pk, sn = ps;
-    if (i + 1 < n_in) load_row(r_in + 1, pu, pk, ps);
-    if (i >= n_in) un = kn = sn = f4(0.0f);  // drain: outputs that depend on these are not stored
+  load_row(y0 - d, pu, pk, ps);
+  auto body = [&](auto parity, int r_in) {
+    const float4 un = pu, kn = pk, sn = ps;
+    if (r_in + 1 < r_end) load_row(r_in + 1, pu, pk, ps);
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
-    pipe.template step<decltype(phase)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
-                                                     sn, out, packed);
-    const int ro = r_in - 2 * d + 1;
+    pipe.template step<decltype(parity)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
+                                                      sn, out, packed);
+    const int ro = r_in - d;
     if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, a.vec, out, packed);
   };
-  int i = 0;
-  for (; i + 2 < n_it; i += 3) {  // unrolled by 3: window slots are compile-time constants
-    body(Int<0>{}, i);
-    body(Int<1>{}, i + 1);
-    body(Int<2>{}, i + 2);
+  int r_in = y0 - d;
+  for (; r_in + 1 < r_end; r_in += 2) {  // unrolled by 2: register slots alternate by parity
+    body(Int<0>{}, r_in);
+    body(Int<1>{}, r_in + 1);
   }
-  if (i < n_it) body(Int<0>{}, i);
-  if (i + 1 < n_it) body(Int<1>{}, i + 1);
+  if (r_in < r_end) body(Int<0>{}, r_in);
 }
 
 template <int K, bool BF>
@@ -576,48 +601,43 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
 
   Pipe<K, BF> pipe;
   pipe.init(face, lane);
-  const int n_it = skew_iterations(y1 - y0, d);  // nrows input iterations + the drain
   int failed_at = -1;
-  auto body = [&](auto phase, int i) -> bool {
+  auto body = [&](auto parity, int i) -> bool {
     const int r_in = r_first + i;
-    float4 kn = f4(0.0f), un = f4(0.0f), sn = f4(0.0f);
-    if (i < nrows) {
-      const int slot = i & (R - 1);
-      if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i / R) & 1u, a.wait_limit)) {
-        failed_at = i;
-        return false;
-      }
-      const unsigned char* srow = ring + (size_t)slot * SL::BYTES;
-      const bool rin = periodic || (r_in >= 0 && r_in < ny);
-      kn = IO::sk4(srow + SL::K_OFF, kofs);
-      if (lc.kb == 1) kn = f4(kn.x);
-      if (lc.kb == 2) kn = f4(kn.w);
-      if (rin && lc.cin4) {
-        un = IO::su4(srow, own);
-        if (a.src) sn = IO::sk4(srow + SL::S_OFF, own);
-      }
-      __syncwarp();
-      // Every lane has read the slot: refill it with row r_in + R.
-      if (i + R < nrows)
-        issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
-                      (a.inject_on && r_in + R == a.inject_row) ? 16u : 0u);
+    const int slot = i & (R - 1);
+    if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i / R) & 1u, a.wait_limit)) {
+      failed_at = i;
+      return false;
     }
+    const unsigned char* srow = ring + (size_t)slot * SL::BYTES;
+    const bool rin = periodic || (r_in >= 0 && r_in < ny);
+    float4 kn = IO::sk4(srow + SL::K_OFF, kofs);
+    if (lc.kb == 1) kn = f4(kn.x);
+    if (lc.kb == 2) kn = f4(kn.w);
+    float4 un = f4(0.0f), sn = f4(0.0f);
+    if (rin && lc.cin4) {
+      un = IO::su4(srow, own);
+      if (a.src) sn = IO::sk4(srow + SL::S_OFF, own);
+    }
+    __syncwarp();
+    // Every lane has read the slot: refill it with row r_in + R.
+    if (i + R < nrows)
+      issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
+                    (a.inject_on && r_in + R == a.inject_row) ? 16u : 0u);
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
-    pipe.template step<decltype(phase)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
-                                                     sn, out, packed);
-    const int ro = r_in - 2 * d + 1;
+    pipe.template step<decltype(parity)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
+                                                      sn, out, packed);
+    const int ro = r_in - d;
     if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, true, out, packed);
     return true;
   };
   int i = 0;
-  for (; i + 2 < n_it; i += 3) {  // unrolled by 3: window slots are compile-time constants
+  for (; i + 1 < nrows; i += 2) {  // unrolled by 2: register slots alternate by parity
     if (!body(Int<0>{}, i)) break;
     if (!body(Int<1>{}, i + 1)) break;
-    if (!body(Int<2>{}, i + 2)) break;
   }
-  if (failed_at < 0 && i < n_it) body(Int<0>{}, i);
-  if (failed_at < 0 && i + 1 < n_it) body(Int<1>{}, i + 1);
+  if (failed_at < 0 && i < nrows) body(Int<0>{}, i);
   if (failed_at >= 0) {
     // Record the timeout, then give every row still in flight (issued but not
     // consumed) one more bounded wait so no copy targets this CTA's shared
