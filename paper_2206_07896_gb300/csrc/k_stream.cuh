@@ -133,6 +133,15 @@ struct Io<true> {
 
 __device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
 
+// Periodic wrap of an index that is usually within one period of [0, n):
+// a compare or two instead of an integer division.
+__device__ __forceinline__ int wrap_near(int i, int n) {
+  if (i >= 0 && i < n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i < 2 * n) return i - n;
+  return wrap_index(i, n);
+}
+
 template <int V>
 struct Int {
   static constexpr int value = V;
@@ -216,6 +225,19 @@ __device__ __forceinline__ float2 madd2(float2 h, float2 acc, float2 ds) {
 #else
   return __ffma2_rn(h, acc, ds);
 #endif
+}
+
+// BF16-Kahan rounding of two step results at once: hi = rn(v), cmp =
+// rn(hi - v), value hi - cmp; the same operations as kahan_round, with packed
+// conversions and differences.  words: (hi | cmp << 16) per cell.
+__device__ __forceinline__ float2 kahan_round2(float2 v, uint2& words) {
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+  const float2 hif = __bfloat1622float2(hi);
+  const __nv_bfloat162 cm = __floats2bfloat162_rn(hif.x - v.x, hif.y - v.y);
+  const float2 cmf = __bfloat1622float2(cm);
+  const unsigned hb = *reinterpret_cast<const unsigned*>(&hi), cb = *reinterpret_cast<const unsigned*>(&cm);
+  words = make_uint2(__byte_perm(hb, cb, 0x5410), __byte_perm(hb, cb, 0x7632));
+  return make_float2(hif.x - cmf.x, hif.y - cmf.y);
 }
 
 // The K-level pipeline of one warp strip, in flux form.
@@ -306,10 +328,10 @@ struct Pipe {
         float4 v = cat4(add2(lo2(C), madd2(h2, accl, lo2(ds))), add2(hi2(C), madd2(h2, acch, hi2(ds))));
         uint4 pk = make_uint4(0, 0, 0, 0);
         if (BF) {
-          float e0, e1, e2, e3;
-          pk = make_uint4(kahan_round(v.x, e0), kahan_round(v.y, e1), kahan_round(v.z, e2),
-                          kahan_round(v.w, e3));
-          v = make_float4(e0, e1, e2, e3);
+          uint2 wl, wh;
+          const float2 el = kahan_round2(lo2(v), wl), eh = kahan_round2(hi2(v), wh);
+          pk = make_uint4(wl.x, wl.y, wh.x, wh.y);
+          v = cat4(el, eh);
         }
         if (!periodic) {  // Dirichlet ghosts stay at zero
           if (rho < 0 || rho >= ny) v = f4(0.0f);
@@ -378,12 +400,14 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
 
   auto load_row = [&](int r, float4& U, float4& Kp, float4& S) {
     bool rin = periodic || (r >= 0 && r < ny);
-    int rr = periodic ? wrap_index(r, ny) : clamp_index(r, ny);
+    int rr = periodic ? wrap_near(r, ny) : clamp_index(r, ny);
     size_t row = (size_t)rr * nx;
     if (a.vec) {
       float4 k4 = IO::k4(a.kappa, row + lc.xv);
-      if (lc.kb == 1) k4 = f4(k4.x);
-      if (lc.kb == 2) k4 = f4(k4.w);
+      if (!periodic) {  // Dirichlet ghost lanes take kappa of the edge cell
+        if (lc.kb == 1) k4 = f4(k4.x);
+        if (lc.kb == 2) k4 = f4(k4.w);
+      }
       Kp = k4;
       if (rin && lc.cin4) {
         U = COH ? IO::u4_cg(a.u_in, row + lc.xv) : IO::u4(a.u_in, row + lc.xv);
@@ -566,7 +590,7 @@ __device__ __forceinline__ void issue_row(const StreamArgs& a, const CopyPlan& c
   const bool rin = periodic || (r >= 0 && r < a.ny);
   if (lane == 0) mbar_arrive_expect_tx(bar, cp.kappa_bytes + (rin ? cp.us_bytes : 0u) + extra_bytes);
   if (cp.active && (rin || cp.field == 0)) {
-    const int rr = periodic ? wrap_index(r, a.ny) : clamp_index(r, a.ny);
+    const int rr = periodic ? wrap_near(r, a.ny) : clamp_index(r, a.ny);
     const size_t g = (size_t)rr * a.nx + cp.col;
     const size_t eb = cp.field == 1 ? Io<BF>::U_BYTES : Io<BF>::KS_BYTES;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -582,6 +606,7 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
   using IO = Io<BF>;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int R = a.stages;
+  const int lgR = __ffs(R) - 1;  // R is a power of two
   // shared memory: [row rings of all warps][mbarriers][face rings of all warps]
   unsigned char* ring = smem + (size_t)wib * R * SL::BYTES;
   unsigned char* bar_base = smem + (size_t)nwarps * R * SL::BYTES;
@@ -620,15 +645,17 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
   auto body = [&](auto parity, int i) -> bool {
     const int r_in = r_first + i;
     const int slot = i & (R - 1);
-    if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i / R) & 1u, a.wait_limit)) {
+    if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i >> lgR) & 1u, a.wait_limit)) {
       failed_at = i;
       return false;
     }
     const unsigned char* srow = ring + (size_t)slot * SL::BYTES;
     const bool rin = periodic || (r_in >= 0 && r_in < ny);
     float4 kn = IO::sk4(srow + SL::K_OFF, kofs);
-    if (lc.kb == 1) kn = f4(kn.x);
-    if (lc.kb == 2) kn = f4(kn.w);
+    if (!periodic) {  // Dirichlet ghost lanes take kappa of the edge cell
+      if (lc.kb == 1) kn = f4(kn.x);
+      if (lc.kb == 2) kn = f4(kn.w);
+    }
     float4 un = f4(0.0f), sn = f4(0.0f);
     if (rin && lc.cin4) {
       un = IO::su4(srow, own);
@@ -660,7 +687,7 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
     if (lane == 0) atomicExch(&g_stream_status, (int)CPB_ERR_TIMEOUT);
     const int last = min(nrows, failed_at + R);
     for (int j = failed_at; j < last; ++j)
-      mbar_wait_bounded(&bars[j & (R - 1)], (uint32_t)(j / R) & 1u, a.wait_limit);
+      mbar_wait_bounded(&bars[j & (R - 1)], (uint32_t)(j >> lgR) & 1u, a.wait_limit);
     __syncwarp();
   }
 }
