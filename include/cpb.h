@@ -205,7 +205,11 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
  * Sec. IV "Fetch task queue" and "Runtime Optimizations").  Grids with at
  * least team_cells cells run on a whole CTA, smaller ones on one warp.
  * Each grid's result is written to its u_out; its u_in is clobbered (used as
- * the ping-pong buffer).  Every grid advances at temporal depth 4.
+ * the ping-pong buffer).  Every grid advances at temporal depth 4.  Grids
+ * whose u_in, u_out, kappa and src are 16-byte aligned with nx % 4 == 0 and
+ * nx >= 128 stream their rows through a per-warp TMA ring (bounded waits, as
+ * in the variant-1 single-grid kernel); the others load rows with ordinary
+ * 128-bit or scalar loads.
  *
  * cpb_batch_order (host): validates the host copy of the descriptors and
  * writes the queue order into h_order[ngrids]: large grids first, each class
@@ -215,8 +219,12 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
  * memory of cpb_batch_work_bytes() bytes (queue counters + status word), reset
  * by the call itself (the call is one memset + one kernel launch, so it can be
  * captured in a CUDA graph).  plan == NULL or plan->blocks <= 0 fills the GPU.
- * cpb_batch_status: synchronises `stream` and returns the status word
- * (CPB_SUCCESS, or CPB_ERR_INVALID_VALUE if a device descriptor was invalid). */
+ * cpb_batch_status: synchronises `stream` and returns the status word:
+ * CPB_SUCCESS; CPB_ERR_INVALID_VALUE if a device descriptor was invalid (that
+ * grid is skipped, the others are complete); or CPB_ERR_TIMEOUT if a TMA-ring
+ * wait expired in some warp (that warp redid the item with ordinary loads and
+ * left the ring for the rest of the launch: every output is still complete).
+ * The first error recorded wins. */
 typedef struct {
   void* u_in;
   void* u_out;

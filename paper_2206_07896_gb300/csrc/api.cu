@@ -567,8 +567,9 @@ cpb_status cpb_stencil_batched(const cpb_grid_desc* d_descs, const int* d_order,
     CPB_TRY(batch_blocks_per_sm(p.threads, &per_sm));
     blocks = std::max(1, per_sm) * device_sm_count();
   }
+  const BatchDebug dbg{g_wait_limit, g_inject_on, g_inject_row};
   return from_cuda(launch_batch(d_descs, d_order, ngrids, n_large, (int)bc, p.grain, blocks, p.threads,
-                                d_work, reinterpret_cast<cudaStream_t>(stream)));
+                                dbg, d_work, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 cpb_status cpb_batch_status(const int* d_work, int* status, cpb_stream_t stream) {

@@ -75,8 +75,16 @@ namespace cpb {
 int batch_threads_max();
 int batch_depth();
 cudaError_t batch_blocks_per_sm(int threads, int* out);
+// Bounded-wait limit of the TMA row ring and the test-only missing-bytes
+// injection (see StreamPass), passed to the batched kernel by value.
+struct BatchDebug {
+  int wait_limit;
+  int inject_on;
+  int inject_row;
+};
 cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
-                         int grain, int blocks, int threads, int* work, cudaStream_t s);
+                         int grain, int blocks, int threads, const BatchDebug& dbg, int* work,
+                         cudaStream_t s);
 }  // namespace cpb
 
 namespace cpb {

@@ -25,6 +25,7 @@ namespace {
 
 constexpr int BATCH_K = 4;
 constexpr int BATCH_MAX_THREADS = 384;
+constexpr int BATCH_STAGES = 2;  // TMA ring slots per warp
 
 // Depth of pass i of a grid with S steps at depth K, with the pass count made
 // odd (split the last pass, or, if it has depth 1, the one before it).
@@ -83,9 +84,11 @@ __device__ __forceinline__ void team_sync() {
 }
 
 // Run all steps of one grid with a team: the whole CTA (CTA = true) or one warp.
+// sm: this warp's row ring, mbarriers and face ring; tma_ok: the warp's ring
+// is usable (cleared for the rest of the launch if a bounded wait expired).
 template <bool CTA>
 __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int lane, int* status,
-                         float4* face) {
+                         const BulkSmem<BATCH_K, false>& sm, bool& tma_ok, const BatchDebug& dbg) {
   if (!desc_ok(g)) {
     if (lane == 0 && wib == 0) atomicExch(status, (int)CPB_ERR_INVALID_VALUE);
     return;
@@ -113,10 +116,13 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
                        reinterpret_cast<uintptr_t>(g.kappa) | reinterpret_cast<uintptr_t>(g.src);
   a.vec = (nx % 4 == 0) && (al % 16 == 0);
   a.n_strips = (nx + OW - 1) / OW;
-  a.stages = 0;
-  a.wait_limit = 0;
-  a.inject_on = 0;
-  a.inject_row = 0;
+  a.stages = BATCH_STAGES;
+  a.wait_limit = dbg.wait_limit;
+  a.inject_on = dbg.inject_on;
+  a.inject_row = dbg.inject_row;
+  // Rows through the TMA ring when the grid allows it (see bulk_eligible in
+  // api.cu); otherwise each lane loads its row slices itself.
+  const bool bulk = a.vec && nx >= 128;
   const int P = npasses(S, BATCH_K);
   const void* src_buf = g.u_in;
   for (int i = 0; i < P; ++i) {
@@ -126,8 +132,18 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
     a.depth = pass_depth(i, S, BATCH_K);
     a.chunk_rows = team_chunk_rows(ny, a.n_strips, nw, a.depth);
     a.n_items = a.n_strips * ((ny + a.chunk_rows - 1) / a.chunk_rows);
-    for (int it = wib; it < a.n_items; it += nw)
-      stream_item<BATCH_K, false, true>(a, it, lane, face);
+    for (int it = wib; it < a.n_items; it += nw) {
+      if (bulk && tma_ok) {
+        tma_ok = bulk_item<BATCH_K, false, false>(a, it, lane, sm.ring, sm.bars, sm.face, status);
+        if (!tma_ok)  // a wait expired (status set): redo this item without the ring
+          stream_item<BATCH_K, false, true>(a, it, lane, sm.face);
+      } else {
+        stream_item<BATCH_K, false, true>(a, it, lane, sm.face);
+      }
+    }
+    // This pass's ordinary stores must be visible to the next pass's bulk
+    // copies (async proxy) before the team moves on.
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     team_sync<CTA>();
     src_buf = dst;
   }
@@ -135,12 +151,13 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
 
 __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
     batch_kernel(const cpb_grid_desc* __restrict__ descs, const int* __restrict__ order, int ngrids,
-                 int n_large, int bc, int grain, int* work) {
+                 int n_large, int bc, int grain, BatchDebug dbg, int* work) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ int s_first;
   extern __shared__ __align__(128) unsigned char smem[];
-  // this warp's ring of per-row face terms (see Pipe in k_stream.cuh)
-  float4* face = reinterpret_cast<float4*>(smem + (size_t)wib * face_ring_rows(BATCH_K) * FACE_SLOT_BYTES);
+  // this warp's row ring, mbarriers and ring of per-row face terms (k_stream.cuh)
+  const BulkSmem<BATCH_K, false> sm(smem, wib, nw, BATCH_STAGES);
+  bool tma_ok = true;
   // Phase 1: large grids, one CTA per grid, fetched `grain` at a time.
   for (;;) {
     if (threadIdx.x == 0) s_first = atomicAdd(&work[0], grain);
@@ -151,7 +168,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
     const int last = min(first + grain, n_large);
     for (int q = first; q < last; ++q) {
       const cpb_grid_desc g = descs[order[q]];
-      run_grid<true>(g, bc, wib, nw, lane, &work[2], face);
+      run_grid<true>(g, bc, wib, nw, lane, &work[2], sm, tma_ok, dbg);
     }
   }
   // Phase 2: small grids, one warp per grid.
@@ -164,7 +181,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
     const int last = min(first + grain, n_small);
     for (int q = first; q < last; ++q) {
       const cpb_grid_desc g = descs[order[n_large + q]];
-      run_grid<false>(g, bc, 0, 1, lane, &work[2], face);
+      run_grid<false>(g, bc, 0, 1, lane, &work[2], sm, tma_ok, dbg);
     }
   }
 }
@@ -176,7 +193,7 @@ int batch_depth() { return BATCH_K; }
 
 namespace {
 unsigned g_batch_attr_done;
-size_t batch_smem(int threads) { return (size_t)(threads / 32) * face_ring_rows(BATCH_K) * FACE_SLOT_BYTES; }
+size_t batch_smem(int threads) { return stream_smem_bytes(false, BATCH_K, threads / 32, 1, BATCH_STAGES); }
 }  // namespace
 
 cudaError_t batch_blocks_per_sm(int threads, int* out) {
@@ -186,14 +203,15 @@ cudaError_t batch_blocks_per_sm(int threads, int* out) {
 }
 
 cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
-                         int grain, int blocks, int threads, int* work, cudaStream_t s) {
+                         int grain, int blocks, int threads, const BatchDebug& dbg, int* work,
+                         cudaStream_t s) {
   const size_t shm = batch_smem(threads);
   cudaError_t e = ensure_smem_optin((const void*)batch_kernel, g_batch_attr_done, shm);
   if (e != cudaSuccess) return e;
   (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
   e = cudaMemsetAsync(work, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  batch_kernel<<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, work);
+  batch_kernel<<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, dbg, work);
   return cudaGetLastError();
 }
 

@@ -479,6 +479,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile(
       "{\n\t.reg .b64 st;\n\t"
@@ -598,22 +602,21 @@ __device__ __forceinline__ void issue_row(const StreamArgs& a, const CopyPlan& c
   }
 }
 
+// One warp item of one pass through this warp's row ring (`ring`, a.stages
+// slots), its mbarriers (`bars`) and face ring (`face`).  Returns false if a
+// bounded wait expired: *status is set to CPB_ERR_TIMEOUT (if still 0), the
+// ring is drained and its mbarriers are left as they are (the caller must not
+// use the ring again).  On success the mbarriers are invalidated, so the next
+// item may initialise them afresh.
 template <int K, bool BF, bool FULL>
-__device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* smem) {
+__device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lane, unsigned char* ring,
+                                          uint64_t* bars, float4* face, int* status) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   using SL = Slot<BF>;
   using IO = Io<BF>;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int R = a.stages;
   const int lgR = __ffs(R) - 1;  // R is a power of two
-  // shared memory: [row rings of all warps][mbarriers][face rings of all warps]
-  unsigned char* ring = smem + (size_t)wib * R * SL::BYTES;
-  unsigned char* bar_base = smem + (size_t)nwarps * R * SL::BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(bar_base) + wib * R;
-  float4* face = reinterpret_cast<float4*>(bar_base + (size_t)nwarps * R * sizeof(uint64_t) +
-                                           (size_t)wib * face_ring_rows(K) * FACE_SLOT_BYTES);
-  const int item = blockIdx.x * nwarps + wib;
   const int nx = a.nx, ny = a.ny, d = FULL ? K : a.depth;
   const bool periodic = a.bc == BC_PERIODIC;
   const int strip = item % a.n_strips, chunk = item / a.n_strips;
@@ -645,6 +648,9 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
   auto body = [&](auto parity, int i) -> bool {
     const int r_in = r_first + i;
     const int slot = i & (R - 1);
+    // The lanes poll converged (one try_wait per poll for the whole warp), so
+    // they reach the same verdict; a warp vote here would make that explicit
+    // but costs registers the pipeline needs (measured: -9%).
     if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i >> lgR) & 1u, a.wait_limit)) {
       failed_at = i;
       return false;
@@ -684,23 +690,49 @@ __device__ __forceinline__ void bulk_item(const StreamArgs& a, unsigned char* sm
     // Record the timeout, then give every row still in flight (issued but not
     // consumed) one more bounded wait so no copy targets this CTA's shared
     // memory after it exits.
-    if (lane == 0) atomicExch(&g_stream_status, (int)CPB_ERR_TIMEOUT);
+    if (lane == 0) atomicCAS(status, 0, (int)CPB_ERR_TIMEOUT);
     const int last = min(nrows, failed_at + R);
     for (int j = failed_at; j < last; ++j)
       mbar_wait_bounded(&bars[j & (R - 1)], (uint32_t)(j >> lgR) & 1u, a.wait_limit);
     __syncwarp();
+    return false;
   }
+  // Every issued row was consumed, so no copy is in flight.
+  __syncwarp();
+  if (lane == 0)
+    for (int j = 0; j < R; ++j) mbar_inval(&bars[j]);
+  __syncwarp();
+  return true;
 }
+
+// Shared memory of a CTA of `nwarps` warps using the row ring:
+// [row rings of all warps][mbarriers of all warps][face rings of all warps].
+template <int K, bool BF>
+struct BulkSmem {
+  unsigned char* ring;
+  uint64_t* bars;
+  float4* face;
+  __device__ __forceinline__ BulkSmem(unsigned char* smem, int wib, int nwarps, int R) {
+    using SL = Slot<BF>;
+    ring = smem + (size_t)wib * R * SL::BYTES;
+    unsigned char* bar_base = smem + (size_t)nwarps * R * SL::BYTES;
+    bars = reinterpret_cast<uint64_t*>(bar_base) + wib * R;
+    face = reinterpret_cast<float4*>(bar_base + (size_t)nwarps * R * sizeof(uint64_t) +
+                                     (size_t)wib * face_ring_rows(K) * FACE_SLOT_BYTES);
+  }
+};
 
 template <int K, bool BF>
 __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int item = blockIdx.x * nwarps + wib;
   if (item >= a.n_items) return;  // warp-uniform; no block-level barrier is used
+  const BulkSmem<K, BF> sm(smem, wib, nwarps, a.stages);
   if (a.depth == K)
-    bulk_item<K, BF, true>(a, smem);
+    bulk_item<K, BF, true>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status);
   else
-    bulk_item<K, BF, false>(a, smem);
+    bulk_item<K, BF, false>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status);
 }
 
 // ---------------------------------------------------------------------------

@@ -152,3 +152,38 @@ def test_batched_graph_capture(dev):
         for g, o in zip(grids, off):
             ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, W.DIRICHLET, "f32")
             np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref)
+
+
+def test_batched_ring_timeout_falls_back_and_is_reported(dev):
+    # One row's copies never complete (test hook) with a short wait limit:
+    # the warps that meet it report CPB_ERR_TIMEOUT, redo the item with
+    # ordinary loads, and every grid's result is still exact.
+    L = cpb.lib(fma=False)
+    grids = [W.random_grid(40 + i, nx, ny, st, W.PERIODIC)
+             for i, (nx, ny, st) in enumerate([(256, 40, 9), (128, 30, 6), (512, 20, 5), (96, 50, 7)])]
+    u, k, s, off = pack(grids, dev)
+    plan = {"grain": 1, "blocks": 2, "threads": 128, "team_cells": 6000}
+    uo = torch.full_like(u, -1.0)
+    uin = u.clone()
+    descs = cpb.batch_descriptors(uin, uo, k, s, off, [g.nx for g in grids],
+                                  [g.ny for g in grids], [g.steps for g in grids],
+                                  [g.dt for g in grids])
+    order, n_large = L.cpb_batch_order(descs, plan)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+    try:
+        L.cpb_debug_set(2000, 7)
+        L.cpb_stencil_batched(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, W.PERIODIC, plan,
+                              work)
+        assert L.cpb_batch_status(work) == cpb.CPB_ERR_TIMEOUT
+    finally:
+        L.cpb_debug_set(0, -1)
+    out = uo.cpu().numpy()
+    for g, o in zip(grids, off):
+        ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, W.PERIODIC, "f32")
+        np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref)
+    # the next launch, without the hook, is clean
+    uin.copy_(u)
+    L.cpb_stencil_batched(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, W.PERIODIC, plan, work)
+    assert L.cpb_batch_status(work) == 0
