@@ -41,9 +41,11 @@ inline size_t bulk_smem_bytes(bool bf16, int warps, int stages) {
 }
 
 // Dynamic shared memory of one CTA of the stream kernels: per warp a ring of
-// k + 1 rows of per-row face terms (3 x 32 float4), plus the variant-1 row ring.
+// (k + 2) & ~1 rows (k + 1 rounded up to even) of per-row face terms
+// (3 x 32 float4), plus the variant-1 row ring.
 inline size_t stream_smem_bytes(bool bf16, int k, int warps, int variant, int stages) {
-  return (size_t)warps * (k + 1) * 3 * 32 * 16 + (variant == 1 ? bulk_smem_bytes(bf16, warps, stages) : 0);
+  return (size_t)warps * ((k + 2) & ~1) * 3 * 32 * 16 +
+         (variant == 1 ? bulk_smem_bytes(bf16, warps, stages) : 0);
 }
 
 // One pass of instantiated depth k (1..8) over the whole grid.

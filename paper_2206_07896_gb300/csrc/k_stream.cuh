@@ -186,9 +186,11 @@ __device__ __forceinline__ LaneCols lane_cols(int xs, int nx, bool periodic) {
 constexpr int FACE_FE = 0, FACE_FN = 1, FACE_DS = 2;
 constexpr int FACE_SLOT_BYTES = 3 * 32 * 16;
 
-// Rows the face ring must hold for depth k: level k reads row r_in - k, the
-// newest row written is r_in.
-__host__ __device__ constexpr int face_ring_rows(int k) { return k + 1; }
+// Rows of the face ring for depth k: level k reads row r_in - k and the
+// newest row written is r_in, so k + 1 rows are needed; rounded up to even so
+// that a row loop unrolled by the ring length keeps both the register parity
+// and every face-ring slot a compile-time constant.
+__host__ __device__ constexpr int face_ring_rows(int k) { return (k + 2) & ~1; }
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
@@ -279,23 +281,30 @@ struct Pipe {
   }
 
   __device__ __forceinline__ float4& at(int slot, int field) { return ring[(slot * 3 + field) * 32]; }
+
+  // Face-ring slot of the row n rows above the input row.  SLOT >= 0: the
+  // input row's slot is the compile-time constant SLOT (the caller's row loop
+  // is unrolled by RF and leaves slot_in untouched); SLOT < 0: slot_in.
+  template <int SLOT>
   __device__ __forceinline__ int back(int n) const {
-    int sl = slot_in - n;
+    if (SLOT >= 0) return (SLOT - n + 2 * RF) % RF;
+    const int sl = slot_in - n;
     return sl < 0 ? sl + RF : sl;
   }
 
   // Consume input row r_in at iteration parity P.  Leaves level d's row
   // r_in - d in `out` (and, for BF16-Kahan storage, its packed words in
-  // `packed`).  FULL: d == K.
-  template <int P, bool FULL>
+  // `packed`).  FULL: d == K.  SLOT: see back().
+  template <int P, bool FULL, int SLOT = -1>
   __device__ __forceinline__ void step(int r_in, int d, int ny, bool periodic, const LaneCols& lc,
                                        float dt, float hdt, float4 un, float4 kn, float4 sn,
                                        float4& out, uint4& packed) {
     constexpr int Q = 1 - P;
     const float kx_e = __shfl_down_sync(CPB_FULL, kn.x, 1);
-    at(slot_in, FACE_FE) = make_float4(kn.x + kn.y, kn.y + kn.z, kn.z + kn.w, kn.w + kx_e);
-    at(slot_in, FACE_DS) = make_float4(dt * sn.x, dt * sn.y, dt * sn.z, dt * sn.w);
-    at(back(1), FACE_FN) = make_float4(kprev.x + kn.x, kprev.y + kn.y, kprev.z + kn.z, kprev.w + kn.w);
+    at(back<SLOT>(0), FACE_FE) = make_float4(kn.x + kn.y, kn.y + kn.z, kn.z + kn.w, kn.w + kx_e);
+    at(back<SLOT>(0), FACE_DS) = make_float4(dt * sn.x, dt * sn.y, dt * sn.z, dt * sn.w);
+    at(back<SLOT>(1), FACE_FN) =
+        make_float4(kprev.x + kn.x, kprev.y + kn.y, kprev.z + kn.z, kprev.w + kn.w);
     kprev = kn;
     U[0][P] = un;
     const float2 h2 = make_float2(hdt, hdt);
@@ -306,7 +315,7 @@ struct Pipe {
       if (FULL || t <= d) {
         const int rho = r_in - t;
         const float4 C = U[t - 1][Q], N = U[t - 1][P];
-        const int sl = back(t);
+        const int sl = back<SLOT>(t);
         const float4 fe = at(sl, FACE_FE), fn = at(sl, FACE_FN), ds = at(sl, FACE_DS);
         // east-face fluxes of the lane's 4 cells; the west flux of the first
         // cell is the east flux of the lane to the west
@@ -346,7 +355,7 @@ struct Pipe {
       }
     }
     out = nw;
-    slot_in = (slot_in + 1 == RF) ? 0 : slot_in + 1;
+    if (SLOT < 0) slot_in = (slot_in + 1 == RF) ? 0 : slot_in + 1;
   }
 };
 
@@ -483,40 +492,51 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+// The helpers below take shared-memory addresses (32-bit, shared window);
+// the pointer forms convert once.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile(
       "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
       "r"(bytes)
       : "memory");
 }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  mbar_arrive_expect_tx(smem_addr(bar), bytes);
+}
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
 
 // Bounded wait for phase `parity` of an mbarrier.  Returns false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit) {
   for (int i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit) {
+  return mbar_wait_bounded(smem_addr(bar), parity, limit);
+}
 
 // One TMA bulk copy global -> this CTA's shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
       : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  bulk_g2s(smem_addr(dst), src, bytes, smem_addr(bar));
 }
 
 // Ring slot geometry.  A slot holds SW cells of u, kappa and s of one row,
@@ -602,36 +622,60 @@ __device__ __forceinline__ void issue_row(const StreamArgs& a, const CopyPlan& c
   }
 }
 
+// Rows J .. N-1 of an unrolled group, in order, stopping at the first that
+// fails: f(parity, slot, i) with both constants known at compile time.
+template <int J, int N, class F>
+__device__ __forceinline__ bool rows_unrolled(F& f, int i) {
+  if constexpr (J == N) {
+    return true;
+  } else {
+    if (!f(Int<J & 1>{}, Int<J>{}, i + J)) return false;
+    return rows_unrolled<J + 1, N>(f, i);
+  }
+}
+
 // One warp item of one pass through this warp's row ring (`ring`, a.stages
-// slots), its mbarriers (`bars`) and face ring (`face`).  Returns false if a
-// bounded wait expired: *status is set to CPB_ERR_TIMEOUT (if still 0), the
-// ring is drained and its mbarriers are left as they are (the caller must not
-// use the ring again).  On success the mbarriers are invalidated, so the next
-// item may initialise them afresh.
-template <int K, bool BF, bool FULL>
-__device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lane, unsigned char* ring,
-                                          uint64_t* bars, float4* face, int* status) {
+// slots), its mbarriers (`bars`) and face ring (`face`), for one boundary
+// rule.  Returns false if a bounded wait expired: *status is set to
+// CPB_ERR_TIMEOUT (if still 0), the ring is drained and its mbarriers are left
+// as they are (the caller must not use the ring again).  On success the
+// mbarriers are invalidated, so the next item may initialise them afresh.
+//
+// The row loop is unrolled by the face-ring length RF (even), so register
+// parities and face-ring slots are constants; the last nrows % RF rows take
+// the same body with run-time face slots.  Periodic refills walk a per-lane
+// source pointer row by row (one compare for the wrap) and expect a constant
+// byte count; Dirichlet refills go through issue_row (ghost rows).
+template <int K, bool BF, bool FULL, bool PERIODIC>
+__device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int lane, unsigned char* ring,
+                                             uint64_t* bars, float4* face, int* status) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
+  constexpr bool periodic = PERIODIC;
   using SL = Slot<BF>;
   using IO = Io<BF>;
+  constexpr int RF = Pipe<K, BF>::RF;
   const int R = a.stages;
   const int lgR = __ffs(R) - 1;  // R is a power of two
   const int nx = a.nx, ny = a.ny, d = FULL ? K : a.depth;
-  const bool periodic = a.bc == BC_PERIODIC;
   const int strip = item % a.n_strips, chunk = item / a.n_strips;
   const int x0 = strip * OW - HALO;
   const int x0a = x0 & ~(SL::ALIGN - 1);  // floor to ALIGN (x0 may be negative)
   const LaneCols lc = lane_cols(x0 + 4 * lane, nx, periodic);
   const int y0 = chunk * a.chunk_rows;
   const int y1 = min(y0 + a.chunk_rows, ny);
-  const bool lane_out = lane >= HALO / 4 && lane < (HALO + OW) / 4;
+  // Lanes that store: inside the strip's output columns and the grid.
+  const bool lane_store = lane >= HALO / 4 && lane < (HALO + OW) / 4 && lc.xs < nx;
   const int r_first = y0 - d, r_end = y1 + d, nrows = r_end - r_first;
   // Slot offsets (cells) of this lane's 4 cells and of the edge access that
   // supplies kappa to a Dirichlet ghost lane.
   const int own = x0 - x0a + 4 * lane;
   const int kofs = lc.kb ? lc.xv - x0a : own;
   const CopyPlan cp = make_copy_plan<BF>(a, x0a, lane);
+  const uint32_t ring_s = smem_addr(ring), bars_s = smem_addr(bars);
+  // Refill at iteration i issues row r_first + i + R; the test hook's row
+  // (if any) is refilled at iteration inject_i.
+  const int inject_i = a.inject_on ? a.inject_row - r_first - R : -0x7fffffff;
 
   if (lane == 0) {
     for (int i = 0; i < R; ++i) mbar_init(&bars[i], 1);
@@ -641,17 +685,27 @@ __device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lan
   for (int i = 0; i < R && i < nrows; ++i)
     issue_row<BF>(a, cp, r_first + i, lane, ring + (size_t)i * SL::BYTES, &bars[i],
                   (a.inject_on && r_first + i == a.inject_row) ? 16u : 0u);
+  // Periodic refill cursor of this lane's copy: wrapped row and its source.
+  const size_t row_bytes = (size_t)nx * (cp.field == 1 ? SL::UB : SL::KB);
+  int next_row = 0;
+  const unsigned char* next_src = nullptr;
+  if (periodic) {
+    next_row = wrap_index(r_first + R, ny);
+    next_src = cp.src_base + (size_t)next_row * row_bytes + (size_t)cp.col * (cp.field == 1 ? SL::UB : SL::KB);
+  }
+  const uint32_t tx_periodic = cp.kappa_bytes + cp.us_bytes;
 
   Pipe<K, BF> pipe;
   pipe.init(face, lane);
   int failed_at = -1;
-  auto body = [&](auto parity, int i) -> bool {
+  auto body = [&](auto parity, auto slot_c, int i) -> bool {
+    constexpr int SLOT = decltype(slot_c)::value;
     const int r_in = r_first + i;
     const int slot = i & (R - 1);
     // The lanes poll converged (one try_wait per poll for the whole warp), so
     // they reach the same verdict; a warp vote here would make that explicit
     // but costs registers the pipeline needs (measured: -9%).
-    if (!mbar_wait_bounded(&bars[slot], (uint32_t)(i >> lgR) & 1u, a.wait_limit)) {
+    if (!mbar_wait_bounded(bars_s + 8u * slot, (uint32_t)(i >> lgR) & 1u, a.wait_limit)) {
       failed_at = i;
       return false;
     }
@@ -669,23 +723,43 @@ __device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lan
     }
     __syncwarp();
     // Every lane has read the slot: refill it with row r_in + R.
-    if (i + R < nrows)
-      issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
-                    (a.inject_on && r_in + R == a.inject_row) ? 16u : 0u);
+    if (i + R < nrows) {
+      if (periodic) {
+        const uint32_t bar = bars_s + 8u * slot;
+        if (lane == 0) mbar_arrive_expect_tx(bar, tx_periodic + (i == inject_i ? 16u : 0u));
+        if (cp.active) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bulk_g2s(ring_s + (uint32_t)(slot * SL::BYTES + cp.dst_off), next_src, cp.bytes, bar);
+        }
+        next_src += row_bytes;
+        if (++next_row == ny) {
+          next_row = 0;
+          next_src -= (size_t)ny * row_bytes;
+        }
+      } else {
+        issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
+                      i == inject_i ? 16u : 0u);
+      }
+    }
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
-    pipe.template step<decltype(parity)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
-                                                      sn, out, packed);
-    const int ro = r_in - d;
-    if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, true, out, packed);
+    pipe.template step<decltype(parity)::value, FULL, SLOT>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un,
+                                                            kn, sn, out, packed);
+    if (i >= 2 * d && lane_store)  // output row r_in - d >= y0
+      store_row<BF>(a.u_out, (size_t)(r_in - d) * nx, lc.xs, nx, true, out, packed);
     return true;
   };
   int i = 0;
-  for (; i + 1 < nrows; i += 2) {  // unrolled by 2: register slots alternate by parity
-    if (!body(Int<0>{}, i)) break;
-    if (!body(Int<1>{}, i + 1)) break;
+  for (; i + RF <= nrows; i += RF)
+    if (!rows_unrolled<0, RF>(body, i)) break;
+  if (failed_at < 0) {
+    // pipe.slot_in is still 0 = i mod RF: the run-time slots take over here
+    for (; i + 1 < nrows; i += 2) {
+      if (!body(Int<0>{}, Int<-1>{}, i)) break;
+      if (!body(Int<1>{}, Int<-1>{}, i + 1)) break;
+    }
+    if (failed_at < 0 && i < nrows) body(Int<0>{}, Int<-1>{}, i);
   }
-  if (failed_at < 0 && i < nrows) body(Int<0>{}, i);
   if (failed_at >= 0) {
     // Record the timeout, then give every row still in flight (issued but not
     // consumed) one more bounded wait so no copy targets this CTA's shared
@@ -703,6 +777,13 @@ __device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lan
     for (int j = 0; j < R; ++j) mbar_inval(&bars[j]);
   __syncwarp();
   return true;
+}
+
+template <int K, bool BF, bool FULL>
+__device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lane, unsigned char* ring,
+                                          uint64_t* bars, float4* face, int* status) {
+  if (a.bc == BC_PERIODIC) return bulk_item_bc<K, BF, FULL, true>(a, item, lane, ring, bars, face, status);
+  return bulk_item_bc<K, BF, FULL, false>(a, item, lane, ring, bars, face, status);
 }
 
 // Shared memory of a CTA of `nwarps` warps using the row ring:
