@@ -64,19 +64,21 @@ def stream_source_hash() -> str:
 
 
 def recorded_traffic(tuning, nx, ny):
-    """DRAM bytes per launch of the stream kernel from the committed ncu record,
-    scaled to this grid by cell count; None if the kernel sources or the tuning
-    changed since the counters were taken."""
+    """DRAM bytes per launch of the stream kernel from the committed ncu record
+    (profiles/stream_traffic.json: one entry per captured tuning), scaled to
+    this grid by cell count; None if the kernel sources changed since the
+    counters were taken or no entry has this depth, variant and warps per CTA."""
     p = os.path.join(ROOT, "profiles", "stream_traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
     if rec.get("source_sha256") != stream_source_hash():
         return None
-    t = rec.get("tuning", {})
-    if any(int(t.get(key, -1)) != int(tuning.get(key, -2)) for key in ("k", "variant", "warps_per_block")):
-        return None
-    return float(rec["dram_bytes_per_cell"]) * nx * ny
+    for e in rec.get("entries", []):
+        t = e.get("tuning", {})
+        if all(int(t.get(key, -1)) == int(tuning.get(key, -2)) for key in ("k", "variant", "warps_per_block")):
+            return float(e["dram_bytes_per_cell"]) * nx * ny
+    return None
 
 
 def dist_env():

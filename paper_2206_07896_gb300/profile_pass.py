@@ -1,0 +1,39 @@
+"""One full-depth pass of the tuned stream kernel per tuning, for profilers.
+
+    python -m paper_2206_07896_gb300.profile_pass N K:chunk:wpb:variant:stages [...]
+
+Builds the N x N periodic FP32 workload (the seeded generator of the scale
+runs), then launches, for each tuning given, ONE pass of depth K through
+cpb_stencil_launch_tuned, so a profiler capturing `-k regex:stream -c <count>`
+sees exactly one launch per tuning.  Prints one line and exits 0.
+"""
+import sys
+
+
+def main(argv):
+    import torch
+
+    import workloads as W
+    from . import lib
+
+    n = int(argv[0]) if argv and ":" not in argv[0] else 4096
+    specs = [a for a in argv if ":" in a] or ["4:256:1:1:2"]
+    L = lib(True)
+    g = W.plain_scale(seed=1, n=n, steps=16)
+    dev = torch.device("cuda")
+    u = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy(g.src).to(dev)
+    out = torch.empty_like(u)
+    for sp in specs:
+        K, c, w, v, st = (int(x) for x in sp.split(":"))
+        t = {"k": K, "chunk_rows": c, "warps_per_block": w, "variant": v, "stages": st}
+        L.cpb_stencil_launch_tuned(u, out, k, s, n, n, K, float(g.dt), g.bc, 0, tuning=t)
+    torch.cuda.synchronize()
+    status = L.cpb_device_status()
+    print("profile_pass", n, specs, "status", status)
+    return 0 if status == 0 else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))
