@@ -21,6 +21,9 @@ Functions (all numpy in, numpy out):
 * ``heat_sum_*``                      FP64 sums.
 * ``adjoint_f64``                     gradient of 0.5||u_T - target||^2 w.r.t.
                                       u_0 and kappa (discrete adjoint, checkpointed).
+* ``strip_warp``                      the shuffle-based temporal-blocked strip
+                                      kernel run with nested warp / lane loops
+                                      split at every shuffle (Sec. III-B).
 * ``vecadd`` / ``dynamic_reverse`` / ``fetch_accounting``
                                       the paper's example kernels (Listings 1-3)
                                       and runtime accounting, to test the executor.
@@ -70,6 +73,8 @@ def lib():
         L.orc_sample_f64.argtypes = [_dp, _dp, _dp, i, i, i, d, i, _i64, i, _dp]
         L.orc_adjoint_f64.argtypes = [_dp, _dp, _dp, _dp, i, i, i, d, i, i, i, _dp, _dp,
                                       C.POINTER(C.c_double)]
+        L.orc_strip_warp_f32.argtypes = [_fp, _fp, _fp, i, i, i, f, i, i, i, i, i, i, _fp]
+        L.orc_strip_warp_f64.argtypes = [_dp, _dp, _dp, i, i, i, d, i, i, i, i, i, i, _dp]
         L.orc_vecadd.argtypes = [_dp, _dp, _dp, i, i, i, i]
         L.orc_dynamic_reverse.argtypes = [_i32, i, i]
         L.orc_fetch_accounting.argtypes = [i, i, i, i, _i32, C.POINTER(C.c_int)]
@@ -122,6 +127,22 @@ def fission(u, kappa, src, steps, dt, bc, precision="f32", block=(16, 16), pool=
         _check(lib().orc_fission_f32(_c(u, np.float32), _c(kappa, np.float32), _c(src, np.float32),
                                      nx, ny, steps, float(np.float32(dt)), bc, bx, by, pool,
                                      block_per_fetch, out), "fission_f32")
+    return out
+
+
+def strip_warp(u, kappa, src, steps, dt, bc, precision="f32", k=4, chunk=64, warps=1, pool=1,
+               fission=True):
+    """The shuffle-based temporal-blocked strip kernel (a warp per 128-column
+    strip, 4 cells per lane, k time levels per pass) executed per the paper's
+    execution model for kernels with warp-level functions: nested warp / lane
+    loops split at every shuffle (Sec. III-B).  fission=False ignores the
+    split at the shuffles (for the test showing it is needed).  k <= 7."""
+    ny, nx = u.shape
+    T, fn = (np.float64, "orc_strip_warp_f64") if precision == "f64" else (np.float32, "orc_strip_warp_f32")
+    out = np.empty((ny, nx), T)
+    dtv = float(dt) if precision == "f64" else float(np.float32(dt))
+    _check(getattr(lib(), fn)(_c(u, T), _c(kappa, T), _c(src, T), nx, ny, steps, dtv, bc, k, chunk,
+                              warps, pool, 1 if fission else 0, out), fn)
     return out
 
 

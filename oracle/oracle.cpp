@@ -31,6 +31,10 @@
 // 4. An FP64 heat sum, an FP64 discrete adjoint (gradient of
 //    L = 0.5 ||u_T - target||^2 with respect to u_0 and kappa), and a
 //    dependency-cone evaluator for sampled cells of a large run.
+// 5. A shuffle-based, temporal-blocked strip kernel (a warp per 128-column
+//    strip, K time levels per pass) executed the way the paper runs kernels
+//    with warp-level functions: nested loops over the warps of a block and
+//    the 32 lanes of a warp, split at every shuffle (Sec. III-B).
 //
 // Build: g++ -O3 -ffp-contract=off (no FMA contraction: GCC contracts a*b+c
 // by default on aarch64, which would change the rounding order above).
@@ -41,6 +45,7 @@
 #include <cstdint>
 #include <cstring>
 #include <deque>
+#include <limits>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -522,6 +527,194 @@ int count_mpmd(void** p) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp-level kernel: a shuffle-based, temporal-blocked strip kernel executed
+// with nested loops split at every warp function (Sec. III-B: a kernel that
+// uses warp-level features is wrapped in an outer loop over the
+// ceil(block_size / 32) warps of a block and an inner loop over the 32 lanes
+// of a warp, one such nest per code section between warp functions)
+// ---------------------------------------------------------------------------
+// The SPMD kernel, one warp per (strip, chunk) item, blockDim.x = 32 * W:
+//   H = K rounded up to a multiple of 4, OW = 128 - 2H.  The warp's strip
+//   covers the 128 columns x0 .. x0 + 127 with x0 = strip * OW - H; lane l
+//   holds the 4 columns x0 + 4l .. x0 + 4l + 3.  The item's output rows are
+//   [y0, y1) (chunks of `chunk` rows); its input rows y0 - d .. y1 + d - 1.
+//   For each input row r:
+//     load u, kappa, s of the lane's 4 cells of row r.  Periodic: wrap.
+//       Dirichlet: a cell outside the grid is a ghost with u = 0, s = 0 and
+//       the kappa of the nearest in-grid cell.
+//     kW = shfl_up(kappa[3]), kE = shfl_down(kappa[0])          [warp function]
+//     for t = 1 .. d (level t produces row rho = r - t):
+//       uW = shfl_up(L[t-1](rho)[3]), uE = shfl_down(L[t-1](rho)[0])
+//                                                               [warp function]
+//       each of the 4 cells: the canonical update from level t-1's rows
+//       rho - 1, rho, rho + 1; Dirichlet ghost cells stay 0
+//     level d's row r - d is stored where it lies in [y0, y1), in the grid
+//     and in the strip's output columns [x0 + H, x0 + 128 - H).
+//   shfl_up / shfl_down with delta 1 over the full warp: a lane with no
+//   source lane keeps its own value.  Level t of a strip is exact on the
+//   columns [x0 + t, x0 + 128 - t), which contain the output columns.
+// MPMD form: the per-lane values that live across a warp function (the level
+// rows, the kappa and source rows) are replicated into per-lane arrays; the
+// values a warp function exchanges pass through a per-warp array of 32 slots.
+// fission = 0 runs every lane's write and read of an exchange in one lane
+// loop (the warp function ignored), for the test that shows the split is
+// needed.
+template <class T>
+struct WarpLane {
+  // rings indexed by row mod 3 (levels 0 .. K-1) and row mod (K + 2) (inputs)
+  T lev[8][3][4];
+  T kap[10][6];  // kW, k0..k3, kE of a row
+  T src[10][4];
+};
+
+template <class T>
+int strip_warp_mpmd(void** p) {
+  const T* u = *(const T**)p[0];
+  T* uo = *(T**)p[1];
+  const T* k = *(const T**)p[2];
+  const T* s = *(const T**)p[3];
+  const int nx = *(int*)p[4], ny = *(int*)p[5];
+  const T dt = *(T*)p[6], hdt = *(T*)p[7];
+  const int bc = *(int*)p[8], K = *(int*)p[9], d = *(int*)p[10], chunk = *(int*)p[11];
+  const int n_items = *(int*)p[12], fission = *(int*)p[13];
+  const int H = (K + 3) & ~3, OW = 128 - 2 * H;
+  const int n_strips = (nx + OW - 1) / OW;
+  const int n_warps = (block_size.x + 31) / 32;
+  const bool periodic = bc == BC_PERIODIC;
+  const int RK = K + 2;
+  std::vector<WarpLane<T>> lanes(32);
+  T x_a[32], x_b[32];  // exchange slots of one warp function
+
+  // Exchange through the per-warp slots.  fission: every lane writes, then
+  // every lane reads (two lane loops).  Otherwise one lane loop does both,
+  // so a lane reads its east neighbour's slot before that lane has written.
+  auto exchange = [&](auto&& put_a, auto&& put_b, auto&& take) {
+    if (fission) {
+      for (int l = 0; l < 32; ++l) {
+        x_a[l] = put_a(l);
+        x_b[l] = put_b(l);
+      }
+      for (int l = 0; l < 32; ++l) take(l, x_a[l > 0 ? l - 1 : l], x_b[l < 31 ? l + 1 : l]);
+    } else {
+      for (int l = 0; l < 32; ++l) {
+        x_a[l] = put_a(l);
+        x_b[l] = put_b(l);
+        take(l, x_a[l > 0 ? l - 1 : l], x_b[l < 31 ? l + 1 : l]);
+      }
+    }
+  };
+
+  for (int w = 0; w < n_warps; ++w) {  // outer loop: warps of the block
+    const int item = block_index * n_warps + w;
+    if (item >= n_items) continue;
+    const int strip = item % n_strips, ch = item / n_strips;
+    const int x0 = strip * OW - H;
+    const int y0 = ch * chunk, y1 = std::min(y0 + chunk, ny);
+    // Exchange slots start as NaN so a read of an unwritten slot shows.
+    for (int l = 0; l < 32; ++l) x_a[l] = x_b[l] = std::numeric_limits<T>::quiet_NaN();
+    for (int l = 0; l < 32; ++l)
+      for (int t = 0; t < 8; ++t)
+        for (int q = 0; q < 3; ++q)
+          for (int e = 0; e < 4; ++e) lanes[l].lev[t][q][e] = T(0);
+
+    auto col_in = [&](int x) { return periodic || (x >= 0 && x < nx); };
+    auto row_in = [&](int y) { return periodic || (y >= 0 && y < ny); };
+    auto mod = [](int a, int m) { int r = a % m; return r < 0 ? r + m : r; };
+
+    for (int r = y0 - d; r < y1 + d; ++r) {
+      const int slot = mod(r, RK);
+      // Section 1 (lane loop) + kappa exchange: load the input row, then
+      // kW / kE from the lanes to the west / east.
+      auto load = [&](int l) {
+        WarpLane<T>& L = lanes[l];
+        const int rr = periodic ? mod(r, ny) : std::min(std::max(r, 0), ny - 1);
+        for (int e = 0; e < 4; ++e) {
+          const int x = x0 + 4 * l + e;
+          const int xx = periodic ? mod(x, nx) : std::min(std::max(x, 0), nx - 1);
+          const size_t g = (size_t)rr * nx + xx;
+          const bool in = col_in(x) && row_in(r);
+          L.kap[slot][1 + e] = k[g];
+          L.src[slot][e] = in ? s[g] : T(0);
+          L.lev[0][mod(r, 3)][e] = in ? u[g] : T(0);
+        }
+        return T(0);
+      };
+      for (int l = 0; l < 32; ++l) load(l);
+      exchange([&](int l) { return lanes[l].kap[slot][4]; }, [&](int l) { return lanes[l].kap[slot][1]; },
+               [&](int l, T west, T east) {
+                 lanes[l].kap[slot][0] = west;
+                 lanes[l].kap[slot][5] = east;
+               });
+      for (int t = 1; t <= d; ++t) {
+        const int rho = r - t;
+        const int cs = mod(rho, 3), ss = mod(rho - 1, 3), ns = mod(rho + 1, 3);
+        const int ks = mod(rho, RK), kss = mod(rho - 1, RK), kns = mod(rho + 1, RK);
+        // u exchange of level t-1's row rho, then the update (section t).
+        exchange([&](int l) { return lanes[l].lev[t - 1][cs][3]; },
+                 [&](int l) { return lanes[l].lev[t - 1][cs][0]; },
+                 [&](int l, T uWl, T uEl) {
+                   WarpLane<T>& L = lanes[l];
+                   T out[4];
+                   for (int e = 0; e < 4; ++e) {
+                     const int x = x0 + 4 * l + e;
+                     if (!col_in(x) || !row_in(rho)) {
+                       out[e] = T(0);
+                       continue;
+                     }
+                     const T c = L.lev[t - 1][cs][e];
+                     const T kc = L.kap[ks][1 + e];
+                     const T uW = e > 0 ? L.lev[t - 1][cs][e - 1] : uWl;
+                     const T uE = e < 3 ? L.lev[t - 1][cs][e + 1] : uEl;
+                     const T kW = L.kap[ks][e], kE = L.kap[ks][e + 2];
+                     const T uS = L.lev[t - 1][ss][e], uN = L.lev[t - 1][ns][e];
+                     const T kS = L.kap[kss][1 + e], kN = L.kap[kns][1 + e];
+                     out[e] = cell_update<T>(c, uW, uE, uS, uN, kc, kW, kE, kS, kN, L.src[ks][e], dt, hdt);
+                   }
+                   for (int e = 0; e < 4; ++e) L.lev[t][cs][e] = out[e];
+                 });
+      }
+      // Section d+1: store level d's row r - d.
+      const int ro = r - d;
+      if (ro >= y0 && ro < y1) {
+        for (int l = 0; l < 32; ++l) {
+          for (int e = 0; e < 4; ++e) {
+            const int x = x0 + 4 * l + e;
+            if (x >= x0 + H && x < x0 + 128 - H && x >= 0 && x < nx)
+              uo[(size_t)ro * nx + x] = lanes[l].lev[d][mod(ro, 3)][e];
+          }
+        }
+      }
+    }
+  }
+  return 0;
+}
+
+// Runs `steps` steps in passes of depth K (the last pass takes the rest),
+// one launch of the strip kernel per pass, W warps per block.
+template <class T>
+int run_strip_warp(const T* u0, const T* k, const T* s, int nx, int ny, int steps, T dt, int bc, int K,
+                   int chunk, int W, int pool, int fission, T* out) {
+  if (K < 1 || K > 7 || chunk < 1 || W < 1 || W > 32) return 1;
+  size_t n = (size_t)nx * ny;
+  T hdt = T(0.5) * dt;
+  std::vector<T> a(u0, u0 + n), b(n);
+  const int H = (K + 3) & ~3, OW = 128 - 2 * H;
+  const int n_items = ((nx + OW - 1) / OW) * ((ny + chunk - 1) / chunk);
+  for (int done = 0; done < steps;) {
+    int d = std::min(K, steps - done);
+    const T* ua = a.data();
+    T* ub = b.data();
+    void* args[14] = {&ua, &ub, &k, &s, &nx, &ny, &dt, &hdt, &bc, &K, &d, &chunk, (void*)&n_items, &fission};
+    int rc = launch(strip_warp_mpmd<T>, args, Dim3{(n_items + W - 1) / W, 1, 1}, Dim3{32 * W, 1, 1}, 0, pool, 0);
+    if (rc) return rc;
+    a.swap(b);
+    done += d;
+  }
+  std::memcpy(out, a.data(), n * sizeof(T));
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint (FP64)
 // ---------------------------------------------------------------------------
 // Step: u_{n+1} = u_n + dt * D(kappa) u_n + dt * s with D symmetric, so
@@ -763,6 +956,19 @@ int orc_adjoint_f64(const double* u0, const double* k, const double* s, const do
   std::memcpy(grad_u0, lam.data(), n * sizeof(double));
   *loss = L;
   return 0;
+}
+
+// The warp-level strip kernel (K <= 7: level rings hold 8 levels).
+int orc_strip_warp_f32(const float* u0, const float* k, const float* s, int nx, int ny, int steps,
+                       float dt, int bc, int K, int chunk, int warps, int pool, int fission, float* out) {
+  if (nx < 1 || ny < 1 || steps < 0) return 1;
+  return run_strip_warp<float>(u0, k, s, nx, ny, steps, dt, bc, K, chunk, warps, pool, fission, out);
+}
+
+int orc_strip_warp_f64(const double* u0, const double* k, const double* s, int nx, int ny, int steps,
+                       double dt, int bc, int K, int chunk, int warps, int pool, int fission, double* out) {
+  if (nx < 1 || ny < 1 || steps < 0) return 1;
+  return run_strip_warp<double>(u0, k, s, nx, ny, steps, dt, bc, K, chunk, warps, pool, fission, out);
 }
 
 // Executor self-tests.
