@@ -21,6 +21,10 @@ Functions (all numpy in, numpy out):
 * ``heat_sum_*``                      FP64 sums.
 * ``adjoint_f64``                     gradient of 0.5||u_T - target||^2 w.r.t.
                                       u_0 and kappa (discrete adjoint, checkpointed).
+* ``direct3`` / ``fission3``          the 3-D 7-point variant: the plain loop,
+                                      and the z-marching tiled kernel (two
+                                      barriers inside its plane loop) run with
+                                      loop fission.
 * ``strip_warp``                      the shuffle-based temporal-blocked strip
                                       kernel run with nested warp / lane loops
                                       split at every shuffle (Sec. III-B).
@@ -75,6 +79,10 @@ def lib():
                                       C.POINTER(C.c_double)]
         L.orc_strip_warp_f32.argtypes = [_fp, _fp, _fp, i, i, i, f, i, i, i, i, i, i, _fp]
         L.orc_strip_warp_f64.argtypes = [_dp, _dp, _dp, i, i, i, d, i, i, i, i, i, i, _dp]
+        L.orc_direct3_f32.argtypes = [_fp, _fp, _fp, i, i, i, i, f, i, i, _fp]
+        L.orc_direct3_f64.argtypes = [_dp, _dp, _dp, i, i, i, i, d, i, i, _dp]
+        L.orc_fission3_f32.argtypes = [_fp, _fp, _fp, i, i, i, i, f, i, i, i, i, i, _fp]
+        L.orc_fission3_f64.argtypes = [_dp, _dp, _dp, i, i, i, i, d, i, i, i, i, i, _dp]
         L.orc_vecadd.argtypes = [_dp, _dp, _dp, i, i, i, i]
         L.orc_dynamic_reverse.argtypes = [_i32, i, i]
         L.orc_fetch_accounting.argtypes = [i, i, i, i, _i32, C.POINTER(C.c_int)]
@@ -143,6 +151,29 @@ def strip_warp(u, kappa, src, steps, dt, bc, precision="f32", k=4, chunk=64, war
     dtv = float(dt) if precision == "f64" else float(np.float32(dt))
     _check(getattr(lib(), fn)(_c(u, T), _c(kappa, T), _c(src, T), nx, ny, steps, dtv, bc, k, chunk,
                               warps, pool, 1 if fission else 0, out), fn)
+    return out
+
+
+def direct3(u, kappa, src, steps, dt, bc, precision="f32", pool=1):
+    """The 3-D 7-point update as a plain loop over cells; arrays [nz, ny, nx]."""
+    nz, ny, nx = u.shape
+    T, fn = (np.float64, "orc_direct3_f64") if precision == "f64" else (np.float32, "orc_direct3_f32")
+    out = np.empty((nz, ny, nx), T)
+    dtv = float(dt) if precision == "f64" else float(np.float32(dt))
+    _check(getattr(lib(), fn)(_c(u, T), _c(kappa, T), _c(src, T), nx, ny, nz, steps, dtv, bc, pool, out),
+           fn)
+    return out
+
+
+def fission3(u, kappa, src, steps, dt, bc, precision="f32", block=(32, 8), zchunks=1, pool=1):
+    """The z-marching tiled 3-D kernel (two barriers inside its plane loop)
+    executed with loop fission on the thread pool."""
+    nz, ny, nx = u.shape
+    T, fn = (np.float64, "orc_fission3_f64") if precision == "f64" else (np.float32, "orc_fission3_f32")
+    out = np.empty((nz, ny, nx), T)
+    dtv = float(dt) if precision == "f64" else float(np.float32(dt))
+    _check(getattr(lib(), fn)(_c(u, T), _c(kappa, T), _c(src, T), nx, ny, nz, steps, dtv, bc, block[0],
+                              block[1], zchunks, pool, out), fn)
     return out
 
 

@@ -35,6 +35,8 @@
 //    strip, K time levels per pass) executed the way the paper runs kernels
 //    with warp-level functions: nested loops over the warps of a block and
 //    the 32 lanes of a warp, split at every shuffle (Sec. III-B).
+// 6. The 3-D 7-point variant: a direct loop and a z-marching tiled kernel
+//    with two barriers inside its plane loop, run with loop fission.
 //
 // Build: g++ -O3 -ffp-contract=off (no FMA contraction: GCC contracts a*b+c
 // by default on aarch64, which would change the rounding order above).
@@ -715,6 +717,211 @@ int run_strip_warp(const T* u0, const T* k, const T* s, int nx, int ny, int step
 }
 
 // ---------------------------------------------------------------------------
+// 3-D 7-point variant (the paper's hotspot3D class) and its z-marching tiled
+// kernel with two barriers inside a loop
+// ---------------------------------------------------------------------------
+// Canonical 3-D update (a stated reading, the 2-D update with a third pair of
+// faces): D = (i, j, k-1), U = (i, j, k+1),
+//   acc = ((fW + fE) + (fS + fN)) + (fD + fU),   u' = c + (hdt * acc + dt * s)
+// with the same face fluxes and boundary rules as in 2-D.  Layout
+// u[k][j][i], x fastest.
+template <class T>
+inline T cell_update3(T c, const T un[6], const T kn[6], T kc, T s, T dt, T hdt) {
+  T f[6];
+  for (int q = 0; q < 6; ++q) f[q] = (kc + kn[q]) * (un[q] - c);
+  T acc = ((f[0] + f[1]) + (f[2] + f[3])) + (f[4] + f[5]);
+  return c + (hdt * acc + dt * s);
+}
+
+// u and kappa seen across the face from a cell towards (ii, jj, kk).
+template <class T>
+inline void neighbour3(const T* u, const T* k, int nx, int ny, int nz, int bc, int ii, int jj, int kk,
+                       T kc, T& un, T& kn) {
+  if (bc == BC_PERIODIC) {
+    size_t g = ((size_t)wrap(kk, nz) * ny + wrap(jj, ny)) * nx + wrap(ii, nx);
+    un = u[g];
+    kn = k[g];
+  } else if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) {
+    un = T(0);
+    kn = kc;
+  } else {
+    size_t g = ((size_t)kk * ny + jj) * nx + ii;
+    un = u[g];
+    kn = k[g];
+  }
+}
+
+template <class T>
+void direct3_planes(const T* u, T* uo, const T* k, const T* s, int nx, int ny, int nz, T dt, T hdt,
+                    int bc, int k0, int k1) {
+  const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+  for (int kk = k0; kk < k1; ++kk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t c = ((size_t)kk * ny + j) * nx + i;
+        T kc = k[c], un[6], kn[6];
+        for (int q = 0; q < 6; ++q)
+          neighbour3(u, k, nx, ny, nz, bc, i + di[q], j + dj[q], kk + dk[q], kc, un[q], kn[q]);
+        uo[c] = cell_update3<T>(u[c], un, kn, kc, s[c], dt, hdt);
+      }
+}
+
+template <class T>
+int direct3_band_mpmd(void** p) {
+  const T* u = *(const T**)p[0];
+  T* uo = *(T**)p[1];
+  const T* k = *(const T**)p[2];
+  const T* s = *(const T**)p[3];
+  int nx = *(int*)p[4], ny = *(int*)p[5], nz = *(int*)p[6];
+  T dt = *(T*)p[7], hdt = *(T*)p[8];
+  int bc = *(int*)p[9], band = *(int*)p[10];
+  int k0 = block_index * band, k1 = std::min(nz, k0 + band);
+  direct3_planes<T>(u, uo, k, s, nx, ny, nz, dt, hdt, bc, k0, k1);
+  return 0;
+}
+
+template <class T>
+int run_direct3(const T* u0, const T* k, const T* s, int nx, int ny, int nz, int steps, T dt, int bc,
+                int pool, T* out) {
+  size_t n = (size_t)nx * ny * nz;
+  T hdt = T(0.5) * dt;
+  std::vector<T> a(u0, u0 + n), b(n);
+  for (int t = 0; t < steps; ++t) {
+    if (pool <= 1) {
+      direct3_planes<T>(a.data(), b.data(), k, s, nx, ny, nz, dt, hdt, bc, 0, nz);
+    } else {
+      const T* ua = a.data();
+      T* ub = b.data();
+      int band = std::max(1, (nz + 2 * pool - 1) / (2 * pool));
+      void* args[11] = {&ua, &ub, &k, &s, &nx, &ny, &nz, &dt, &hdt, &bc, &band};
+      int rc = launch(direct3_band_mpmd<T>, args, Dim3{(nz + band - 1) / band, 1, 1}, Dim3{1, 1, 1}, 0,
+                      pool, 0);
+      if (rc) return rc;
+    }
+    a.swap(b);
+  }
+  std::memcpy(out, a.data(), n * sizeof(T));
+  return 0;
+}
+
+// The z-marching tiled SPMD kernel (blockDim = (BX, BY), grid = (ceil(nx/BX),
+// ceil(ny/BY), ZC); block (bx, by, bz) owns the column tile and the planes
+// [bz*PZ, min(nz, (bz+1)*PZ)), PZ = ceil(nz / ZC); dynamic shared memory =
+// two (BX+2)*(BY+2) tiles of T).  Each thread keeps its cell's u and kappa of
+// planes k-1, k, k+1 and s of plane k in registers:
+//   prologue: load planes z0 - 1 and z0 (boundary rule for planes outside).
+//   for k = z0 .. z1-1:
+//     R0: load plane k+1 into registers; stage plane k of u and kappa into
+//         the tiles (edge threads also stage the in-plane halo cell in their
+//         direction, boundary rule as in 2-D)
+//     __syncthreads();
+//     R1: if the cell is in the grid: the update from the tile (in-plane
+//         neighbours) and the registers (planes k-1, k+1); write u_out;
+//         rotate the register planes (k-1 <- k <- k+1)
+//     __syncthreads();
+// MPMD: both barriers sit inside the k loop, so the loop over k is kept and
+// each of its two barrier-free regions becomes one loop over the block's
+// threads; the per-thread register planes live across the barriers and are
+// replicated into per-thread arrays.
+template <class T>
+int stencil3_tile_mpmd(void** p) {
+  const T* u = *(const T**)p[0];
+  T* uo = *(T**)p[1];
+  const T* k = *(const T**)p[2];
+  const T* s = *(const T**)p[3];
+  const int nx = *(int*)p[4], ny = *(int*)p[5], nz = *(int*)p[6];
+  const T dt = *(T*)p[7], hdt = *(T*)p[8];
+  const int bc = *(int*)p[9];
+  const int BX = block_size.x, BY = block_size.y, TW = BX + 2, TH = BY + 2;
+  const int gx = grid_size.x, gy = grid_size.y, ZC = grid_size.z;
+  const int bx = block_index % gx, by = (block_index / gx) % gy, bz = block_index / (gx * gy);
+  const int PZ = (nz + ZC - 1) / ZC, z0 = bz * PZ, z1 = std::min(nz, z0 + PZ);
+  if (z0 >= z1) return 0;
+  T* su = (T*)dynamic_shared_memory;
+  T* sk = su + (size_t)TW * TH;
+  const int nthreads = BX * BY;
+  const bool periodic = bc == BC_PERIODIC;
+  // per-thread register planes: u and kappa of planes k-1, k, k+1
+  std::vector<T> um(nthreads), uc(nthreads), up(nthreads), km(nthreads), kc(nthreads), kp(nthreads);
+  // Value of (gi, gj, kk) under the boundary rule: Dirichlet ghosts have u = 0
+  // and kappa of the nearest in-grid cell.
+  auto fetch = [&](int gi, int gj, int kk, T& uv, T& kv) {
+    if (periodic) {
+      size_t g = ((size_t)wrap(kk, nz) * ny + wrap(gj, ny)) * nx + wrap(gi, nx);
+      uv = u[g];
+      kv = k[g];
+    } else {
+      bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny && kk >= 0 && kk < nz;
+      int ci = std::min(std::max(gi, 0), nx - 1), cj = std::min(std::max(gj, 0), ny - 1);
+      int ck = std::min(std::max(kk, 0), nz - 1);
+      uv = in ? u[((size_t)kk * ny + gj) * nx + gi] : T(0);
+      kv = k[((size_t)ck * ny + cj) * nx + ci];
+    }
+  };
+  auto stage = [&](int gi, int gj, int kk, int slot) { fetch(gi, gj, kk, su[slot], sk[slot]); };
+  // prologue (one region, no barrier yet)
+  for (int tid = 0; tid < nthreads; ++tid) {
+    int gi = bx * BX + tid % BX, gj = by * BY + tid / BX;
+    fetch(gi, gj, z0 - 1, um[tid], km[tid]);
+    fetch(gi, gj, z0, uc[tid], kc[tid]);
+  }
+  for (int kk = z0; kk < z1; ++kk) {
+    // R0
+    for (int tid = 0; tid < nthreads; ++tid) {
+      int tx = tid % BX, ty = tid / BX;
+      int gi = bx * BX + tx, gj = by * BY + ty;
+      fetch(gi, gj, kk + 1, up[tid], kp[tid]);
+      int c = (ty + 1) * TW + (tx + 1);
+      su[c] = uc[tid];
+      sk[c] = kc[tid];
+      if (tx == 0) stage(gi - 1, gj, kk, c - 1);
+      if (tx == BX - 1) stage(gi + 1, gj, kk, c + 1);
+      if (ty == 0) stage(gi, gj - 1, kk, c - TW);
+      if (ty == BY - 1) stage(gi, gj + 1, kk, c + TW);
+    }
+    // __syncthreads()
+    // R1
+    for (int tid = 0; tid < nthreads; ++tid) {
+      int tx = tid % BX, ty = tid / BX;
+      int gi = bx * BX + tx, gj = by * BY + ty;
+      if (gi < nx && gj < ny) {
+        int c = (ty + 1) * TW + (tx + 1);
+        size_t g = ((size_t)kk * ny + gj) * nx + gi;
+        const T un[6] = {su[c - 1], su[c + 1], su[c - TW], su[c + TW], um[tid], up[tid]};
+        const T kn[6] = {sk[c - 1], sk[c + 1], sk[c - TW], sk[c + TW], km[tid], kp[tid]};
+        uo[g] = cell_update3<T>(su[c], un, kn, sk[c], s[g], dt, hdt);
+      }
+      um[tid] = uc[tid];
+      km[tid] = kc[tid];
+      uc[tid] = up[tid];
+      kc[tid] = kp[tid];
+    }
+    // __syncthreads(): the next R0 overwrites the tiles
+  }
+  return 0;
+}
+
+template <class T>
+int run_fission3(const T* u0, const T* k, const T* s, int nx, int ny, int nz, int steps, T dt, int bc,
+                 int bx, int by, int zc, int pool, T* out) {
+  size_t n = (size_t)nx * ny * nz;
+  T hdt = T(0.5) * dt;
+  std::vector<T> a(u0, u0 + n), b(n);
+  Dim3 grid{(nx + bx - 1) / bx, (ny + by - 1) / by, zc};
+  size_t shm = 2 * sizeof(T) * (size_t)(bx + 2) * (by + 2);
+  for (int t = 0; t < steps; ++t) {
+    const T* ua = a.data();
+    T* ub = b.data();
+    void* args[10] = {&ua, &ub, &k, &s, &nx, &ny, &nz, &dt, &hdt, &bc};
+    int rc = launch(stencil3_tile_mpmd<T>, args, grid, Dim3{bx, by, 1}, shm, pool, 0);
+    if (rc) return rc;
+    a.swap(b);
+  }
+  std::memcpy(out, a.data(), n * sizeof(T));
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint (FP64)
 // ---------------------------------------------------------------------------
 // Step: u_{n+1} = u_n + dt * D(kappa) u_n + dt * s with D symmetric, so
@@ -969,6 +1176,31 @@ int orc_strip_warp_f64(const double* u0, const double* k, const double* s, int n
                        double dt, int bc, int K, int chunk, int warps, int pool, int fission, double* out) {
   if (nx < 1 || ny < 1 || steps < 0) return 1;
   return run_strip_warp<double>(u0, k, s, nx, ny, steps, dt, bc, K, chunk, warps, pool, fission, out);
+}
+
+// 3-D 7-point variant.
+int orc_direct3_f32(const float* u0, const float* k, const float* s, int nx, int ny, int nz, int steps,
+                    float dt, int bc, int pool, float* out) {
+  if (nx < 1 || ny < 1 || nz < 1 || steps < 0) return 1;
+  return run_direct3<float>(u0, k, s, nx, ny, nz, steps, dt, bc, pool, out);
+}
+
+int orc_direct3_f64(const double* u0, const double* k, const double* s, int nx, int ny, int nz,
+                    int steps, double dt, int bc, int pool, double* out) {
+  if (nx < 1 || ny < 1 || nz < 1 || steps < 0) return 1;
+  return run_direct3<double>(u0, k, s, nx, ny, nz, steps, dt, bc, pool, out);
+}
+
+int orc_fission3_f32(const float* u0, const float* k, const float* s, int nx, int ny, int nz, int steps,
+                     float dt, int bc, int bx, int by, int zc, int pool, float* out) {
+  if (nx < 1 || ny < 1 || nz < 1 || steps < 0 || bx < 1 || by < 1 || zc < 1) return 1;
+  return run_fission3<float>(u0, k, s, nx, ny, nz, steps, dt, bc, bx, by, zc, pool, out);
+}
+
+int orc_fission3_f64(const double* u0, const double* k, const double* s, int nx, int ny, int nz,
+                     int steps, double dt, int bc, int bx, int by, int zc, int pool, double* out) {
+  if (nx < 1 || ny < 1 || nz < 1 || steps < 0 || bx < 1 || by < 1 || zc < 1) return 1;
+  return run_fission3<double>(u0, k, s, nx, ny, nz, steps, dt, bc, bx, by, zc, pool, out);
 }
 
 // Executor self-tests.

@@ -27,6 +27,11 @@ files are not used -- these seeded fields stand in at the same scale):
 * ``differentiation``  2048 x 2048, kappa~U[0.5,1), u0~U[0,1), s = 0,
                        Dirichlet, r = 0.2, 200 steps, checkpoint every 20;
                        target = sum of 8 seeded sinusoidal modes.
+* ``volume``           the 3-D 7-point variant (the paper's hotspot3D class,
+                       512 x 512 in its evaluation, layer count unstated):
+                       512 x 512 x 512, distributions of ``plain_small``,
+                       Dirichlet, r = 0.15 (six faces: r <= 1/6 keeps the
+                       update a convex combination), 100 steps, seed 5.
 """
 from __future__ import annotations
 
@@ -86,6 +91,54 @@ def random_grid(seed: int, nx: int, ny: int, steps: int, bc: int, r: float = 0.2
         src = np.zeros_like(src)
     return Grid(u, kappa, src.astype(np.float32), dt_for(kappa, r), steps, bc,
                 name=f"random-{nx}x{ny}-seed{seed}")
+
+
+@dataclass
+class Grid3:
+    """One 3-D grid problem.  Fields are (nz, ny, nx) float32, x fastest."""
+    u: np.ndarray
+    kappa: np.ndarray
+    src: np.ndarray
+    dt: np.float32
+    steps: int
+    bc: int
+    name: str = ""
+
+    @property
+    def nx(self) -> int:
+        return int(self.u.shape[2])
+
+    @property
+    def ny(self) -> int:
+        return int(self.u.shape[1])
+
+    @property
+    def nz(self) -> int:
+        return int(self.u.shape[0])
+
+    @property
+    def updates(self) -> int:
+        return self.nx * self.ny * self.nz * self.steps
+
+
+def random_grid3(seed: int, nx: int, ny: int, nz: int, steps: int, bc: int, r: float = 0.15,
+                 kappa_lo: float = 0.5, kappa_hi: float = 1.0, src_hi: float = 1e-3,
+                 zero_source: bool = False) -> Grid3:
+    """A 3-D grid with the plain-small distributions (u, kappa, s drawn in that order)."""
+    rng = np.random.default_rng(seed)
+    u = rng.random((nz, ny, nx), dtype=np.float32)
+    kappa = _uniform(rng, (nz, ny, nx), kappa_lo, kappa_hi)
+    src = rng.random((nz, ny, nx), dtype=np.float32) * np.float32(src_hi)
+    if zero_source:
+        src = np.zeros_like(src)
+    return Grid3(u, kappa, src.astype(np.float32), dt_for(kappa, r), steps, bc,
+                 name=f"random3-{nx}x{ny}x{nz}-seed{seed}")
+
+
+def volume(seed: int = 5, n: int = 512, steps: int = 100) -> Grid3:
+    g = random_grid3(seed, n, n, n, steps, DIRICHLET, r=0.15)
+    g.name = f"volume-{n}x{n}x{n}-dirichlet-{steps}steps"
+    return g
 
 
 def plain_small(seed: int = 0, n: int = 512, steps: int = 100) -> Grid:
