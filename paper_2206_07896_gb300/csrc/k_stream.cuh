@@ -184,7 +184,8 @@ __device__ __forceinline__ LaneCols lane_cols(int xs, int nx, bool periodic) {
 // so program order is the only ordering needed.  Layout per warp:
 // [slot][field][lane] float4, field 0 = faceE, 1 = faceN, 2 = dt*s.
 constexpr int FACE_FE = 0, FACE_FN = 1, FACE_DS = 2;
-constexpr int FACE_SLOT_BYTES = 3 * 32 * 16;
+constexpr int FACE_SLOT_F4 = 3 * 32;  // float4 units per slot
+constexpr int FACE_SLOT_BYTES = FACE_SLOT_F4 * 16;
 
 // Rows of the face ring for depth k: level k reads row r_in - k and the
 // newest row written is r_in, so k + 1 rows are needed; rounded up to even so
@@ -266,7 +267,7 @@ struct Pipe {
   float4 U[K][2];
   float4 G[K][2];
   float4 kprev;
-  float4* ring;  // this lane's slice: ring[(slot * 3 + field) * 32]
+  float4* ring;  // this lane's slice: ring[slot * FACE_SLOT_F4 + field * 32]
   int slot_in;   // face-ring slot of the current input row
 
   static constexpr int RF = face_ring_rows(K);
@@ -280,7 +281,7 @@ struct Pipe {
     for (int i = 0; i < 3 * RF; ++i) ring[i * 32] = f4(0.0f);
   }
 
-  __device__ __forceinline__ float4& at(int slot, int field) { return ring[(slot * 3 + field) * 32]; }
+  __device__ __forceinline__ float4& at(int slot, int field) { return ring[slot * FACE_SLOT_F4 + field * 32]; }
 
   // Face-ring slot of the row n rows above the input row.  SLOT >= 0: the
   // input row's slot is the compile-time constant SLOT (the caller's row loop
@@ -317,8 +318,6 @@ struct Pipe {
         const float4 C = U[t - 1][Q], N = U[t - 1][P];
         const int sl = back<SLOT>(t);
         const float4 fe = at(sl, FACE_FE), fn = at(sl, FACE_FN), ds = at(sl, FACE_DS);
-        // east-face fluxes of the lane's 4 cells; the west flux of the first
-        // cell is the east flux of the lane to the west
         const float uEw = __shfl_down_sync(CPB_FULL, C.x, 1);
         float4 F;
         F.x = fe.x * (C.y - C.x);
@@ -634,6 +633,25 @@ __device__ __forceinline__ bool rows_unrolled(F& f, int i) {
   }
 }
 
+// Rows J, J + 2, .. < N of an unrolled group as pairs f(_, slot, i) with
+// the slot a compile-time constant, stopping at the first that fails.
+template <int J, int N, class F>
+__device__ __forceinline__ bool pairs_unrolled(F& f, int i) {
+  if constexpr (J >= N) {
+    return true;
+  } else {
+    if (!f(Int<0>{}, Int<J>{}, i + J)) return false;
+    return pairs_unrolled<J + 2, N>(f, i);
+  }
+}
+
+// Depths at which the row loop takes rows in pairs: there the level
+// registers already limit a multiprocessor to 8-10 warps, so the extra
+// registers of a pair cost no occupancy and the overlap of two rows hides
+// latency (measured on GB300 at 8192^2: depth 8, 444 -> 390 us per pass); at
+// depth <= 5 a pair needs more than 128 registers and loses 16 -> 11 warps.
+__host__ __device__ constexpr bool rows_in_pairs(int k) { return k >= 6; }
+
 // One warp item of one pass through this warp's row ring (`ring`, a.stages
 // slots), its mbarriers (`bars`) and face ring (`face`), for one boundary
 // rule.  Returns false if a bounded wait expired: *status is set to
@@ -698,60 +716,98 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
   Pipe<K, BF> pipe;
   pipe.init(face, lane);
   int failed_at = -1;
-  auto body = [&](auto parity, auto slot_c, int i) -> bool {
-    constexpr int SLOT = decltype(slot_c)::value;
+  // Wait for input row i (slot i mod R) and read the lane's kappa, u and s.
+  // The lanes poll converged (one try_wait per poll for the whole warp), so
+  // they reach the same verdict; a warp vote here would make that explicit
+  // but costs registers the pipeline needs (measured: -9%).
+  auto fetch = [&](int i, float4& kn, float4& un, float4& sn) -> bool {
     const int r_in = r_first + i;
     const int slot = i & (R - 1);
-    // The lanes poll converged (one try_wait per poll for the whole warp), so
-    // they reach the same verdict; a warp vote here would make that explicit
-    // but costs registers the pipeline needs (measured: -9%).
-    if (!mbar_wait_bounded(bars_s + 8u * slot, (uint32_t)(i >> lgR) & 1u, a.wait_limit)) {
-      failed_at = i;
-      return false;
-    }
+    if (!mbar_wait_bounded(bars_s + 8u * slot, (uint32_t)(i >> lgR) & 1u, a.wait_limit)) return false;
     const unsigned char* srow = ring + (size_t)slot * SL::BYTES;
     const bool rin = periodic || (r_in >= 0 && r_in < ny);
-    float4 kn = IO::sk4(srow + SL::K_OFF, kofs);
+    kn = IO::sk4(srow + SL::K_OFF, kofs);
     if (!periodic) {  // Dirichlet ghost lanes take kappa of the edge cell
       if (lc.kb == 1) kn = f4(kn.x);
       if (lc.kb == 2) kn = f4(kn.w);
     }
-    float4 un = f4(0.0f), sn = f4(0.0f);
+    un = f4(0.0f);
+    sn = f4(0.0f);
     if (rin && lc.cin4) {
       un = IO::su4(srow, own);
       if (a.src) sn = IO::sk4(srow + SL::S_OFF, own);
     }
-    __syncwarp();
-    // Every lane has read the slot: refill it with row r_in + R.
-    if (i + R < nrows) {
-      if (periodic) {
-        const uint32_t bar = bars_s + 8u * slot;
-        if (lane == 0) mbar_arrive_expect_tx(bar, tx_periodic + (i == inject_i ? 16u : 0u));
-        if (cp.active) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          bulk_g2s(ring_s + (uint32_t)(slot * SL::BYTES + cp.dst_off), next_src, cp.bytes, bar);
-        }
-        next_src += row_bytes;
-        if (++next_row == ny) {
-          next_row = 0;
-          next_src -= (size_t)ny * row_bytes;
-        }
-      } else {
-        issue_row<BF>(a, cp, r_in + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
-                      i == inject_i ? 16u : 0u);
+    return true;
+  };
+  // Every lane has read slot i mod R: refill it with row r_first + i + R.
+  auto refill = [&](int i) {
+    if (i + R >= nrows) return;
+    const int slot = i & (R - 1);
+    if (periodic) {
+      const uint32_t bar = bars_s + 8u * slot;
+      if (lane == 0) mbar_arrive_expect_tx(bar, tx_periodic + (i == inject_i ? 16u : 0u));
+      if (cp.active) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_g2s(ring_s + (uint32_t)(slot * SL::BYTES + cp.dst_off), next_src, cp.bytes, bar);
       }
+      next_src += row_bytes;
+      if (++next_row == ny) {
+        next_row = 0;
+        next_src -= (size_t)ny * row_bytes;
+      }
+    } else {
+      issue_row<BF>(a, cp, r_first + i + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
+                    i == inject_i ? 16u : 0u);
     }
+  };
+  // Advance the pipeline by input row i and store the finished row.
+  auto compute = [&](auto parity, auto slot_c, int i, float4 kn, float4 un, float4 sn) {
+    constexpr int SLOT = decltype(slot_c)::value;
+    const int r_in = r_first + i;
     float4 out;
     uint4 packed = make_uint4(0, 0, 0, 0);
     pipe.template step<decltype(parity)::value, FULL, SLOT>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un,
                                                             kn, sn, out, packed);
     if (i >= 2 * d && lane_store)  // output row r_in - d >= y0
       store_row<BF>(a.u_out, (size_t)(r_in - d) * nx, lc.xs, nx, true, out, packed);
+  };
+  auto body = [&](auto parity, auto slot_c, int i) -> bool {
+    float4 kn, un, sn;
+    if (!fetch(i, kn, un, sn)) {
+      failed_at = i;
+      return false;
+    }
+    __syncwarp();
+    refill(i);
+    compute(parity, slot_c, i, kn, un, sn);
+    return true;
+  };
+  // Rows i and i + 1 (i even): both waits first, then one straight-line block
+  // advancing both rows, in which row i + 1's lower levels can overlap row i's
+  // upper levels (the spin-wait loop of a single row ends the scheduler's
+  // block).  A failed wait consumed nothing that the drain below misses.
+  auto pair = [&](auto, auto slot_c, int i) -> bool {
+    constexpr int S0 = decltype(slot_c)::value;
+    float4 k0, u0, s0, k1, u1, s1;
+    if (!fetch(i, k0, u0, s0) || !fetch(i + 1, k1, u1, s1)) {
+      failed_at = i;
+      return false;
+    }
+    __syncwarp();
+    refill(i);
+    refill(i + 1);
+    compute(Int<0>{}, Int<S0>{}, i, k0, u0, s0);
+    compute(Int<1>{}, Int<S0 + 1>{}, i + 1, k1, u1, s1);
     return true;
   };
   int i = 0;
-  for (; i + RF <= nrows; i += RF)
-    if (!rows_unrolled<0, RF>(body, i)) break;
+  if constexpr (rows_in_pairs(K)) {
+    for (; i + RF <= nrows; i += RF)
+      if (!pairs_unrolled<0, RF>(pair, i)) break;
+  } else {
+    for (; i + RF <= nrows; i += RF)
+      if (!rows_unrolled<0, RF>(body, i)) break;
+  }
   if (failed_at < 0) {
     // pipe.slot_in is still 0 = i mod RF: the run-time slots take over here
     for (; i + 1 < nrows; i += 2) {

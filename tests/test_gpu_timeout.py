@@ -24,13 +24,14 @@ def dev():
     return torch.device("cuda:0")
 
 
-def test_wait_timeout_is_reported_and_context_survives(dev):
+@pytest.mark.parametrize("depth", [4, 8])   # single rows / rows in pairs
+def test_wait_timeout_is_reported_and_context_survives(dev, depth):
     L = cpb.lib(fma=False)
-    g = W.random_grid(3, 256, 64, 4, W.PERIODIC)
+    g = W.random_grid(3, 256, 64, depth, W.PERIODIC)
     u = torch.from_numpy(g.u).to(dev)
     k = torch.from_numpy(g.kappa).to(dev)
     s = torch.from_numpy(g.src).to(dev)
-    t = {"k": 4, "chunk_rows": 16, "warps_per_block": 4, "variant": 1, "stages": 4}
+    t = {"k": depth, "chunk_rows": 16, "warps_per_block": 4, "variant": 1, "stages": 4}
     assert L.cpb_device_status() == 0
     out = torch.empty_like(u)
     try:
