@@ -5,8 +5,8 @@ Headline workload (one bench step): the plain FP32 stencil at scale -- one
 at the autotuned temporal-block depth -- followed by the FP64 heat sum of the
 result.  Inputs (4 x 256 MiB) are larger than L2 and resident in HBM when the
 timed region starts.  The other forms of the path (BF16-Kahan storage at
-16384^2, the 4096-grid batch, the adjoint at 2048^2) are reported under
-"forms" when requested with --forms.
+16384^2, the 4096-grid batch, the adjoint at 2048^2, the 3-D 7-point variant
+at 512^3) are reported under "forms" (skipped with --no-forms).
 
 Arms:
   default            the CUDA library (libcpb.so) through its C ABI.
@@ -79,6 +79,18 @@ def recorded_traffic(tuning, nx, ny):
         if all(int(t.get(key, -1)) == int(tuning.get(key, -2)) for key in ("k", "variant", "warps_per_block")):
             return float(e["dram_bytes_per_cell"]) * nx * ny
     return None
+
+
+def time_bounds(cells, k, hbm_gbs, clk):
+    """Lower bounds on one pass of depth k over `cells` cells: HBM bytes at the
+    measured copy rate, and FP32 lane operations (10 per cell-update) on all
+    SMs at the sampled SM clock (or the maximum clock if none was sampled)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    t_hbm = 16.0 * cells / (hbm_gbs * 1e9) * 1e6
+    t_fp32 = 10.0 * cells * k / (sms * 128 * mhz * 1e6) * 1e6
+    return {"hbm": t_hbm, "fp32_lanes": t_fp32, "sms": sms, "sm_mhz": mhz}
 
 
 def dist_env():
@@ -272,6 +284,15 @@ def form_precision(L, cpb, dev, stream, n=16384, steps=2000):
     diff = float((un - ref32).abs().max() / ref32.abs().max())
     upd = N * steps
     hbm, _ = peaks()
+    # The same comparison at depth 2, where both storages are HBM-bound (the
+    # regime in which 12 instead of 16 bytes per cell-update pays).
+    k2 = {"k": 2, "chunk_rows": 256, "warps_per_block": 1, "variant": 1, "stages": 2}
+    ms32_k2 = _time(lambda: L.cpb_stencil_launch_tuned(u, out, k, s, nx, ny, steps, dt, W.DIRICHLET,
+                                                       cpb.CPB_F32, tuning=k2, scratch=sa.view(torch.float32),
+                                                       stream=sh), 1, stream)
+    ms16_k2 = _time(lambda: L.cpb_stencil_launch_tuned(st, so, kb, sb, nx, ny, steps, dt, W.DIRICHLET,
+                                                       cpb.CPB_BF16_KAHAN, tuning=k2, scratch=sa, stream=sh),
+                    1, stream)
     return {"workload": f"precision-{n}x{n}-dirichlet-{steps}steps",
             "f32": {"gcells": upd / ms32 / 1e6, "ms": ms32, "tuning": t32,
                     "effective_gbs_16B": upd * 16 / t32["k"] / ms32 / 1e6},
@@ -279,6 +300,8 @@ def form_precision(L, cpb, dev, stream, n=16384, steps=2000):
                            "effective_gbs_12B": upd * 12 / t16["k"] / ms16 / 1e6,
                            "rel_linf_vs_f32_gpu": diff},
             "speedup_bf16_vs_f32": ms32 / ms16,
+            "at_depth_2": {"f32_gcells": upd / ms32_k2 / 1e6, "bf16_kahan_gcells": upd / ms16_k2 / 1e6,
+                           "speedup_bf16_vs_f32": ms32_k2 / ms16_k2},
             "heat_sum_fp64": {"ms": ms_sum, "gbs": N * 4 / ms_sum / 1e6, "frac_hbm": N * 4 / ms_sum / 1e6 / hbm},
             "note": "error vs the FP64 oracle is measured in tests/test_gpu_precision.py"}
 
@@ -315,6 +338,11 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     d_descs = cpb.to_device_bytes(descs, dev)
     d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
     work = torch.zeros(4, dtype=torch.int32, device=dev)
+    # Grain-size sweep (grids per queue fetch x CTA size), the GPU counterpart
+    # of the paper's average vs aggressive coarse-grained fetching; the timed
+    # run below uses the fastest plan (each run starts from a fresh copy of u).
+    plan, sweep = L.cpb_batch_autotune(d_descs, d_order, bt.ngrids, n_large, cpb.CPB_F32, W.DIRICHLET,
+                                       work, plan, stream=sh)
 
     def run_batch():
         uin.copy_(u)
@@ -342,6 +370,7 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     ms_each = _time(run_each, 1, stream)
     return {"workload": f"batch-{bt.ngrids}-grids-32..1024-steps-10..500", "updates": upd,
             "cells": int(cells.sum()), "n_large": n_large, "plan": plan,
+            "grain_sweep_ms": {f"grain{g}_threads{t}": v for (g, t), v in sweep.items()},
             "batched": {"gcells": upd / ms_b / 1e6, "ms": ms_b, "status": status},
             "one_grid_at_a_time": {"gcells": upd / ms_each / 1e6, "ms": ms_each},
             "speedup_batched_vs_per_grid": ms_each / ms_b}
@@ -380,10 +409,30 @@ def form_adjoint(L, cpb, dev, stream):
                     "central FD needs 2 forwards per direction"}
 
 
+def form_volume(L, cpb, dev, stream, n=512, steps=100):
+    """The 3-D 7-point variant on the 512^3 volume (one launch per step)."""
+    import torch
+    g = W.volume(n=n, steps=steps)
+    sh = stream.cuda_stream
+    u = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy(g.src).to(dev)
+    del g.u, g.kappa, g.src
+    out, scr = torch.empty_like(u), torch.empty_like(u)
+    ms = _time(lambda: L.cpb_stencil3d_launch(u, out, k, s, n, n, n, steps, float(g.dt), g.bc,
+                                              scratch=scr, stream=sh), 2, stream)
+    upd = n ** 3 * steps
+    hbm, _ = peaks()
+    gbs = upd * 16 / ms / 1e6
+    return {"workload": g.name, "gcells": upd / ms / 1e6, "ms": ms, "ms_per_step": ms / steps,
+            "effective_gbs_16B": gbs, "frac_hbm": gbs / hbm,
+            "note": "z-marching tiled kernel, one launch per step, default geometry (32 x 8 threads)"}
+
+
 def measure_forms(L, cpb, dev, stream):
     out = {}
     for name, fn in (("precision", form_precision), ("batched", form_batched),
-                     ("adjoint", form_adjoint)):
+                     ("adjoint", form_adjoint), ("volume", form_volume)):
         try:
             out[name] = fn(L, cpb, dev, stream)
         except Exception as e:  # report, never lose the headline line
@@ -485,6 +534,7 @@ def run_ours(args):
         tmax = per_rank_ms
     value = updates * world / (tmax * 1e-3) / 1e9
 
+    clk = clocks.summary()   # reads (and removes) the sample file once
     # Roofline of the dominant kernel (full-depth stream pass).
     hbm, which = peaks()
     avg_pass = sum(full_pass_ms) / len(full_pass_ms)
@@ -495,6 +545,10 @@ def run_ours(args):
             "kernel": ("stream_bulk_kernel" if tuning.get("variant") == 1 else "stream_kernel")
                       + f"<K={k},f32>", "avg_launch_ms": avg_pass,
             "algorithmic_bytes_per_launch": alg_bytes,
+            # the pass's two time bounds: HBM (16 B per cell at the measured
+            # copy rate) and FP32 lanes (10 FP32 operations per cell-update in
+            # flux form, 128 lanes per SM at the sampled SM clock)
+            "time_bounds_us": time_bounds(nx * ny, k, hbm, clk),
             "effective_cell_rate_vs_k1_roofline": value / world / (hbm * 1e9 / 16 / 1e9)}
 
     # End to end through the C ABI on host buffers (pinned), copies timed.
@@ -540,7 +594,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}",
                            "step": "1000 time steps + FP64 heat sum"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * (n_pass + 2), "clocks": clocks.summary()}
+                "gpu_launches": args.steps * (n_pass + 2), "clocks": clk}
         if forms is not None:
             line["forms"] = forms
         print(json.dumps(line), flush=True)

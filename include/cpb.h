@@ -198,6 +198,27 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
                             cpb_dtype dtype, void* d_workspace, size_t ws_bytes,
                             cpb_stream_t stream);
 
+/* 3-D 7-point variant (the class of the paper's hotspot3D benchmark,
+ * Sec. V): u'(x,y,z) from its six face neighbours, with the faces D (z-1)
+ * and U (z+1) added to the 2-D update and rounded in the order
+ *   acc = ((fW + fE) + (fS + fN)) + (fD + fU),  u' = c + (hdt*acc + dt*s),
+ * f = (kc + kn)(un - c); Dirichlet ghosts u = 0, kappa = kc; periodic wraps
+ * every axis.  CPB_F32 only.  Fields are nz x ny x nx, x fastest, caller-owned
+ * device memory; src may be NULL (s = 0).  Steps run one launch each of the
+ * z-marching tiled kernel (a CTA of 32 x by threads owns 128 columns x by
+ * rows and a run of ceil(nz / grid.z) planes, with a __syncthreads inside its
+ * plane loop), ping-ponging as cpb_stencil_launch does (result always in u_out;
+ * u_in clobbered unless scratch is given).  The caller's launch geometry:
+ * block = (32, by, 1) with 1 <= by <= 8, else CPB_ERR_UNSUPPORTED_CONFIG;
+ * grid = (ceil(nx / 128), ceil(ny / by), zc) with 1 <= zc <= nz, else
+ * CPB_ERR_INVALID_VALUE; shared_bytes >= 2048 * (by + 2), else
+ * CPB_ERR_SHARED_MEM.  block = {0,0,0} selects by = 8 and z-chunks of about
+ * 16 planes.  Validation and errors as
+ * for cpb_stencil_launch; asynchronous on `stream`. */
+cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                                int ny, int nz, int steps, float dt, cpb_boundary bc, cpb_dim3 grid,
+                                cpb_dim3 block, size_t shared_bytes, void* scratch, cpb_stream_t stream);
+
 /* Batched persistent stencil: many independent grids (uneven sizes and step
  * counts, CPB_F32 storage, one boundary rule) advanced in ONE kernel launch.
  * Resident CTAs fetch grids from a device work queue, `grain` grids per atomic
@@ -249,6 +270,29 @@ cpb_status cpb_stencil_batched(const cpb_grid_desc* d_descs, const int* d_order,
                                int n_large, cpb_dtype dtype, cpb_boundary bc,
                                const cpb_batch_plan* plan, int* d_work, cpb_stream_t stream);
 cpb_status cpb_batch_status(const int* d_work, int* status, cpb_stream_t stream);
+
+/* Grain-size selection for the batched launch, the GPU counterpart of the
+ * paper's trade-off between average and aggressive coarse-grained fetching
+ * (Sec. IV "Runtime Optimizations", evaluated in Sec. V "aggressive
+ * coarse-grained fetching"): more grids per atomic fetch means fewer fetches
+ * but a coarser balance of work over the resident CTAs, so the best grain
+ * depends on the batch.  The call times the batch once for every candidate
+ * (grain, threads) in CPB_BATCH_TUNE_GRAINS x CPB_BATCH_TUNE_THREADS, grain
+ * major, with plan->team_cells and one wave of CTAs, re-times the three
+ * fastest twice and writes the fastest plan to *plan (blocks = 0).
+ * ms_table (optional, host, CPB_BATCH_TUNE_CANDIDATES floats) receives the
+ * single-run time of every candidate in milliseconds (-1 where the launch
+ * was rejected).  Arguments as for cpb_stencil_batched, with d_order built
+ * for plan->team_cells.  The batch runs several times: every grid's u_in
+ * and u_out are overwritten, so tune on copies of the fields.  Synchronises
+ * `stream`.  A status word other than CPB_SUCCESS after a run is returned
+ * (the plan is then left unchanged). */
+#define CPB_BATCH_TUNE_GRAINS 5   /* 1, 2, 4, 8, 16 */
+#define CPB_BATCH_TUNE_THREADS 3  /* 128, 256, 384 */
+#define CPB_BATCH_TUNE_CANDIDATES (CPB_BATCH_TUNE_GRAINS * CPB_BATCH_TUNE_THREADS)
+cpb_status cpb_batch_autotune(const cpb_grid_desc* d_descs, const int* d_order, int ngrids,
+                              int n_large, cpb_dtype dtype, cpb_boundary bc, int* d_work,
+                              cpb_stream_t stream, cpb_batch_plan* plan, float* ms_table);
 
 /* Discrete adjoint of the N-step stencil (CPB_F32), for gradients of a loss
  * L(u_T) with respect to u_0 and kappa.  With lambda_T = dL/du_T (given):

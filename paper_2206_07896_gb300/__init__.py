@@ -52,6 +52,12 @@ class cpb_grid_desc(C.Structure):
                 ("dt", C.c_float)]
 
 
+# Candidates of cpb_batch_autotune (include/cpb.h), grain major.
+BATCH_TUNE_GRAINS = (1, 2, 4, 8, 16)
+BATCH_TUNE_THREADS = (128, 256, 384)
+BATCH_TUNE_CANDIDATES = len(BATCH_TUNE_GRAINS) * len(BATCH_TUNE_THREADS)
+
+
 class cpb_batch_plan(C.Structure):
     _fields_ = [("grain", C.c_int), ("blocks", C.c_int), ("threads", C.c_int),
                 ("team_cells", C.c_int)]
@@ -98,6 +104,9 @@ _SIGS = {
     "cpb_batch_work_bytes": (_sz, []),
     "cpb_stencil_batched": (_i, [_vp, _vp, _i, _i, _i, _i, C.POINTER(cpb_batch_plan), _vp, _vp]),
     "cpb_batch_status": (_i, [_vp, C.POINTER(_i), _vp]),
+    "cpb_stencil3d_launch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _f, _i, cpb_dim3, cpb_dim3, _sz,
+                                  _vp, _vp]),
+    "cpb_batch_autotune": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp, C.POINTER(cpb_batch_plan), _vp]),
     "cpb_adjoint_workspace_bytes": (_sz, [_i, _i, _i, _i]),
     "cpb_adjoint_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _vp, _sz, _vp]),
     "cpb_adjoint_backward": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _vp, _vp, _sz, _vp]),
@@ -189,6 +198,12 @@ class Library:
                    float(dt), bc, dtype, _dim3(grid), _dim3(block), shared_bytes, ptr(scratch),
                    stream_handle(stream))
 
+    def cpb_stencil3d_launch(self, u_in, u_out, kappa, src, nx, ny, nz, steps, dt, bc,
+                             grid=(0, 0, 0), block=(0, 0, 0), shared_bytes=0, scratch=None, stream=None):
+        self._call("cpb_stencil3d_launch", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny, nz, steps,
+                   float(dt), bc, _dim3(grid), _dim3(block), shared_bytes, ptr(scratch),
+                   stream_handle(stream))
+
     def cpb_stencil_launch_tuned(self, u_in, u_out, kappa, src, nx, ny, steps, dt, bc, dtype,
                                  tuning=None, scratch=None, stream=None):
         t = C.byref(as_tuning(tuning)) if tuning is not None else None
@@ -273,6 +288,21 @@ class Library:
         st = _i()
         self._call("cpb_batch_status", ptr(d_work), C.byref(st), stream_handle(stream))
         return st.value
+
+    def cpb_batch_autotune(self, d_descs, d_order, ngrids, n_large, dtype, bc, d_work, plan=None,
+                           stream=None):
+        """Returns (best plan dict, {(grain, threads): ms or None}).  Overwrites
+        every grid's u_in and u_out (tune on copies)."""
+        pl = as_plan(plan if plan is not None else self.cpb_batch_plan_default())
+        table = (C.c_float * BATCH_TUNE_CANDIDATES)()
+        self._call("cpb_batch_autotune", ptr(d_descs), ptr(d_order), ngrids, n_large, dtype, bc,
+                   ptr(d_work), stream_handle(stream), C.byref(pl), table)
+        ms = {}
+        for gi, g in enumerate(BATCH_TUNE_GRAINS):
+            for ti, t in enumerate(BATCH_TUNE_THREADS):
+                v = table[gi * len(BATCH_TUNE_THREADS) + ti]
+                ms[(g, t)] = float(v) if v > 0 else None
+        return pl.as_dict(), ms
 
     def cpb_adjoint_workspace_bytes(self, nx, ny, steps, ckpt_every) -> int:
         return self._lib.cpb_adjoint_workspace_bytes(nx, ny, steps, ckpt_every)

@@ -309,6 +309,61 @@ cpb_status cpb_stencil_launch(void* u_in, void* u_out, const void* kappa, const 
   return enqueue_tile(f, nx, ny, steps, dt, bc, grid, block, shared_bytes, s);
 }
 
+cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                                int ny, int nz, int steps, float dt, cpb_boundary bc, cpb_dim3 grid,
+                                cpb_dim3 block, size_t shared_bytes, void* scratch, cpb_stream_t stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || steps < 0) return CPB_ERR_INVALID_VALUE;
+  if ((long long)ny * nz > 0x7fffffffLL) return CPB_ERR_INVALID_VALUE;
+  Fields f{u_in, u_out, kappa, src, scratch};
+  // the checks of the 2-D call on the same bytes (nx x (ny*nz) cells)
+  cpb_status st = check_common(f, nx, ny * nz, steps, dt, bc, CPB_F32);
+  if (st != CPB_SUCCESS) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int gx = (nx + 127) / 128;
+  int by = 8, gz = 0;
+  if (block.x == 0 && block.y == 0 && block.z == 0) {
+    // default: 32 x 8 threads, z-chunks of about 16 planes (measured best at
+    // 512^3 among 8..64-plane chunks: each chunk re-reads two planes, longer
+    // chunks leave too few CTAs)
+    gz = std::max(1, (nz + 15) / 16);
+  } else {
+    if (block.x != 32 || block.y < 1 || block.y > 8 || block.z != 1) return CPB_ERR_UNSUPPORTED_CONFIG;
+    by = (int)block.y;
+    if ((long long)grid.x != gx || (long long)grid.y != (ny + by - 1) / by || grid.z < 1 ||
+        (long long)grid.z > nz)
+      return CPB_ERR_INVALID_VALUE;
+    if (shared_bytes < vol_smem_bytes(by)) return CPB_ERR_SHARED_MEM;
+    gz = (int)grid.z;
+  }
+  const dim3 g3((unsigned)gx, (unsigned)((ny + by - 1) / by), (unsigned)gz);
+  const int vec = (nx % 4 == 0) && aligned(u_in, 16) && aligned(u_out, 16) && aligned(scratch, 16) &&
+                  aligned(kappa, 16) && aligned(src, 16);
+  const size_t ub = (size_t)nx * ny * nz * sizeof(float);
+  if (steps == 0) {
+    CPB_TRY(cudaMemcpyAsync(u_out, u_in, ub, cudaMemcpyDeviceToDevice, s));
+    return CPB_SUCCESS;
+  }
+  bool copy_at_end = false;
+  std::vector<int> depths = pass_depths(steps, 1, scratch != nullptr, &copy_at_end);
+  const int P = (int)depths.size();
+  const void* src_buf = u_in;
+  for (int i = 0; i < P; ++i) {
+    void* dst;
+    if (scratch)
+      dst = ((P - 1 - i) % 2 == 0) ? u_out : scratch;
+    else if (!copy_at_end)
+      dst = ((P - 1 - i) % 2 == 0) ? u_out : u_in;
+    else
+      dst = (i % 2 == 0) ? u_out : u_in;
+    CPB_TRY(launch_vol_f32(static_cast<const float*>(src_buf), static_cast<float*>(dst),
+                           static_cast<const float*>(kappa), static_cast<const float*>(src), nx, ny, nz, dt,
+                           (int)bc, vec, g3, by, s));
+    src_buf = dst;
+  }
+  if (copy_at_end) CPB_TRY(cudaMemcpyAsync(u_out, u_in, ub, cudaMemcpyDeviceToDevice, s));
+  return CPB_SUCCESS;
+}
+
 cpb_status cpb_stencil_launch_tuned(void* u_in, void* u_out, const void* kappa, const void* src,
                                     int nx, int ny, int steps, float dt, cpb_boundary bc,
                                     cpb_dtype dtype, const cpb_tuning* tuning, void* scratch,
@@ -582,6 +637,71 @@ cpb_status cpb_batch_status(const int* d_work, int* status, cpb_stream_t stream)
   CPB_TRY(cudaMemcpyAsync(w, d_work, sizeof(w), cudaMemcpyDeviceToHost, s));
   CPB_TRY(cudaStreamSynchronize(s));
   *status = w[2];
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_batch_autotune(const cpb_grid_desc* d_descs, const int* d_order, int ngrids,
+                              int n_large, cpb_dtype dtype, cpb_boundary bc, int* d_work,
+                              cpb_stream_t stream, cpb_batch_plan* plan, float* ms_table) {
+  if (!plan || !plan_ok(*plan)) return CPB_ERR_INVALID_VALUE;
+  static const int grains[CPB_BATCH_TUNE_GRAINS] = {1, 2, 4, 8, 16};
+  static const int threads[CPB_BATCH_TUNE_THREADS] = {128, 256, 384};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  CPB_TRY(cudaEventCreate(&e0));
+  CPB_TRY(cudaEventCreate(&e1));
+  cpb_status result = CPB_SUCCESS;
+  // Time `reps` back-to-back runs of plan p; -1 if the launch is rejected.
+  auto time_plan = [&](const cpb_batch_plan& p, int reps) -> float {
+    if (cudaEventRecord(e0, s) != cudaSuccess) return -1.0f;
+    for (int r = 0; r < reps; ++r) {
+      const cpb_status st = cpb_stencil_batched(d_descs, d_order, ngrids, n_large, dtype, bc, &p, d_work, stream);
+      if (st != CPB_SUCCESS) {
+        if (result == CPB_SUCCESS && st != CPB_ERR_LAUNCH && st != CPB_ERR_CUDA) result = st;
+        return -1.0f;
+      }
+    }
+    float ms = -1.0f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return -1.0f;
+    int status = 0;
+    if (cpb_batch_status(d_work, &status, stream) != CPB_SUCCESS || status != CPB_SUCCESS) {
+      if (result == CPB_SUCCESS) result = status != CPB_SUCCESS ? (cpb_status)status : CPB_ERR_CUDA;
+      return -1.0f;
+    }
+    return ms / reps;
+  };
+  std::vector<std::pair<float, cpb_batch_plan>> timed;
+  cpb_batch_plan p = *plan;
+  p.blocks = 0;
+  time_plan(p, 1);  // warm-up (first launch sets the shared-memory opt-in)
+  for (int gi = 0; gi < CPB_BATCH_TUNE_GRAINS; ++gi)
+    for (int ti = 0; ti < CPB_BATCH_TUNE_THREADS; ++ti) {
+      p.grain = grains[gi];
+      p.threads = threads[ti];
+      const float ms = result == CPB_SUCCESS ? time_plan(p, 1) : -1.0f;
+      if (ms_table) ms_table[gi * CPB_BATCH_TUNE_THREADS + ti] = ms;
+      if (ms > 0.0f) timed.push_back({ms, p});
+    }
+  std::sort(timed.begin(), timed.end(),
+            [](const std::pair<float, cpb_batch_plan>& a, const std::pair<float, cpb_batch_plan>& b) {
+              return a.first < b.first;
+            });
+  float best = -1.0f;
+  cpb_batch_plan bp = *plan;
+  for (size_t i = 0; i < timed.size() && i < 3 && result == CPB_SUCCESS; ++i) {
+    const float ms = time_plan(timed[i].second, 2);
+    if (ms > 0.0f && (best < 0.0f || ms < best)) {
+      best = ms;
+      bp = timed[i].second;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != CPB_SUCCESS) return result;
+  if (best < 0.0f) return CPB_ERR_LAUNCH;
+  *plan = bp;
   return CPB_SUCCESS;
 }
 

@@ -96,6 +96,14 @@ cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u
 }  // namespace cpb
 
 namespace cpb {
+// 3-D 7-point z-marching kernel (k_vol.cu): one launch per step, block
+// (32, by), grid (ceil(nx / 128), ceil(ny / by), z-chunks).
+size_t vol_smem_bytes(int by);
+cudaError_t launch_vol_f32(const float* u_in, float* u_out, const float* kappa, const float* src, int nx,
+                           int ny, int nz, float dt, int bc, int vec, dim3 grid, int by, cudaStream_t s);
+}  // namespace cpb
+
+namespace cpb {
 // Heat sum with partials in a file-scope device array (k_sum.cu).
 long long heat_sum_noalloc_max_cells();
 cudaError_t launch_heat_sum_noalloc(const void* u, long long n, int dtype, double* d_out,

@@ -187,3 +187,33 @@ def test_batched_ring_timeout_falls_back_and_is_reported(dev):
     uin.copy_(u)
     L.cpb_stencil_batched(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, W.PERIODIC, plan, work)
     assert L.cpb_batch_status(work) == 0
+
+
+def test_batch_autotune_picks_a_measured_plan_that_stays_exact(dev):
+    # Grain-size selection (the GPU counterpart of average vs aggressive
+    # coarse-grained fetching): every candidate is timed, the chosen plan is
+    # one of them, and a run with it is still bit-exact.
+    L = cpb.lib(fma=False)
+    bc = W.DIRICHLET
+    grids = small_batch(17, bc)
+    u, k, s, off = pack(grids, dev)
+    plan0 = {"grain": 1, "blocks": 0, "threads": 384, "team_cells": 4096}
+    # tune on copies: the tuning runs overwrite u_in and u_out
+    tu, to = u.clone(), torch.empty_like(u)
+    descs = cpb.batch_descriptors(tu, to, k, s, off, [g.nx for g in grids], [g.ny for g in grids],
+                                  [g.steps for g in grids], [g.dt for g in grids])
+    order, n_large = L.cpb_batch_order(descs, plan0)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+    best, table = L.cpb_batch_autotune(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, bc, work,
+                                       plan0)
+    assert len(table) == cpb.BATCH_TUNE_CANDIDATES
+    assert all(v is not None and v > 0 for v in table.values())
+    assert (best["grain"], best["threads"]) in table
+    assert best["team_cells"] == plan0["team_cells"] and best["blocks"] == 0
+    uo, _ = run_batch(L, grids, dev, bc, best, u, k, s, off)
+    out = uo.cpu().numpy()
+    for g, o in zip(grids, off):
+        ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, bc, "f32")
+        np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref)
