@@ -211,10 +211,14 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
  * u_in clobbered unless scratch is given).  The caller's launch geometry:
  * block = (32, by, 1) with 1 <= by <= 8, else CPB_ERR_UNSUPPORTED_CONFIG;
  * grid = (ceil(nx / 128), ceil(ny / by), zc) with 1 <= zc <= nz, else
- * CPB_ERR_INVALID_VALUE; shared_bytes >= 2048 * (by + 2), else
- * CPB_ERR_SHARED_MEM.  block = {0,0,0} selects by = 8 and z-chunks of about
+ * CPB_ERR_INVALID_VALUE; shared_bytes >= cpb_stencil3d_shared_bytes(by),
+ * else CPB_ERR_SHARED_MEM.  With nx % 4 == 0 and 16-byte aligned fields the
+ * planes stream through an 8-slot shared-memory ring filled by asynchronous
+ * copies several planes ahead; otherwise each thread loads the next plane
+ * into registers.  block = {0,0,0} selects by = 8 and z-chunks of about
  * 16 planes.  Validation and errors as
  * for cpb_stencil_launch; asynchronous on `stream`. */
+size_t cpb_stencil3d_shared_bytes(int by); /* 0 if by is outside 1..8 */
 cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
                                 int ny, int nz, int steps, float dt, cpb_boundary bc, cpb_dim3 grid,
                                 cpb_dim3 block, size_t shared_bytes, void* scratch, cpb_stream_t stream);

@@ -104,6 +104,7 @@ _SIGS = {
     "cpb_batch_work_bytes": (_sz, []),
     "cpb_stencil_batched": (_i, [_vp, _vp, _i, _i, _i, _i, C.POINTER(cpb_batch_plan), _vp, _vp]),
     "cpb_batch_status": (_i, [_vp, C.POINTER(_i), _vp]),
+    "cpb_stencil3d_shared_bytes": (_sz, [_i]),
     "cpb_stencil3d_launch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _f, _i, cpb_dim3, cpb_dim3, _sz,
                                   _vp, _vp]),
     "cpb_batch_autotune": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp, C.POINTER(cpb_batch_plan), _vp]),
@@ -197,6 +198,9 @@ class Library:
         self._call("cpb_stencil_launch", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny, steps,
                    float(dt), bc, dtype, _dim3(grid), _dim3(block), shared_bytes, ptr(scratch),
                    stream_handle(stream))
+
+    def cpb_stencil3d_shared_bytes(self, by) -> int:
+        return self._lib.cpb_stencil3d_shared_bytes(by)
 
     def cpb_stencil3d_launch(self, u_in, u_out, kappa, src, nx, ny, nz, steps, dt, bc,
                              grid=(0, 0, 0), block=(0, 0, 0), shared_bytes=0, scratch=None, stream=None):

@@ -309,6 +309,8 @@ cpb_status cpb_stencil_launch(void* u_in, void* u_out, const void* kappa, const 
   return enqueue_tile(f, nx, ny, steps, dt, bc, grid, block, shared_bytes, s);
 }
 
+size_t cpb_stencil3d_shared_bytes(int by) { return (by >= 1 && by <= 8) ? vol_smem_bytes(by) : 0; }
+
 cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
                                 int ny, int nz, int steps, float dt, cpb_boundary bc, cpb_dim3 grid,
                                 cpb_dim3 block, size_t shared_bytes, void* scratch, cpb_stream_t stream) {
@@ -322,10 +324,10 @@ cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, cons
   const int gx = (nx + 127) / 128;
   int by = 8, gz = 0;
   if (block.x == 0 && block.y == 0 && block.z == 0) {
-    // default: 32 x 8 threads, z-chunks of about 16 planes (measured best at
-    // 512^3 among 8..64-plane chunks: each chunk re-reads two planes, longer
-    // chunks leave too few CTAs)
-    gz = std::max(1, (nz + 15) / 16);
+    // default: 32 x 8 threads, z-chunks of about 32 planes (measured at 512^3
+    // on GB300 over by = 1..8 and 8..64-plane chunks: by = 8 with 32-64
+    // planes is fastest; each chunk re-reads two planes)
+    gz = std::max(1, (nz + 31) / 32);
   } else {
     if (block.x != 32 || block.y < 1 || block.y > 8 || block.z != 1) return CPB_ERR_UNSUPPORTED_CONFIG;
     by = (int)block.y;

@@ -221,9 +221,175 @@ __global__ void __launch_bounds__(256) vol_kernel(const VolArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Plane-ring kernel (16-byte aligned fields, nx % 4 == 0)
+// ---------------------------------------------------------------------------
+// The register kernel above gives a load one plane of work (~0.1 us) to
+// arrive, far less than the memory latency, so every plane stalls.  Here each
+// CTA keeps a ring of VR plane slots in shared memory, filled by per-thread
+// asynchronous copies (cp.async, 16 bytes per copy; 4 bytes for the x-halo
+// cells), one commit group per plane, up to VR - 3 planes ahead of the plane
+// being updated.  A slot holds, for one plane: u and kappa of the tile's
+// by + 2 rows (the y-halo rows included), s of its by rows and the x-halo
+// cells (u, kappa) of its by rows.  The boundary rules map onto the copies:
+// a Dirichlet ghost u (or s) is a zero-filled copy (source size 0), a ghost
+// kappa is copied from the clamped position (the ghost columns beyond nx read
+// column nx - 1 at update time), periodic copies read the wrapped position.
+// Per plane z:  wait for this thread's copies up to plane z + 1; barrier (all
+// copies visible, and every thread has finished plane z - 1, so the slot of
+// plane z - 2 is free); issue plane z + VR - 2 into that slot; update plane z
+// from the slots of planes z - 1, z and z + 1.  One barrier per plane.
+constexpr int VR = 8;  // ring slots
+
+__host__ __device__ constexpr int vring_slot_floats(int by) { return (3 * by + 4) * 128 + 4 * by; }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copy the 4 cells x0 .. x0+3 of row (y, z) of u and kappa (and s when
+// with_s) into a slot row under the boundary rule.
+__device__ __forceinline__ void ring_row(const VolArgs& a, int x0, int y, int z, float* du, float* dk,
+                                         float* ds) {
+  size_t g, gk;
+  bool in = true;
+  if (a.bc == BC_PERIODIC) {
+    g = gk = vidx(a, wrap_index(x0, a.nx), wrap_index(y, a.ny), wrap_index(z, a.nz));
+  } else {
+    const int xc = x0 < a.nx ? x0 : a.nx - 4;
+    in = x0 < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz;
+    g = gk = vidx(a, xc, clamp_index(y, a.ny), clamp_index(z, a.nz));
+  }
+  cp_async16(du, a.u + g, in ? 16 : 0);
+  cp_async16(dk, a.k + gk, 16);
+  if (ds) cp_async16(ds, a.s ? a.s + g : a.k + gk, (a.s && in && y < a.ny && z < a.nz) ? 16 : 0);
+}
+
+__device__ __forceinline__ void ring_cell(const VolArgs& a, int x, int y, int z, float* du, float* dk) {
+  size_t g;
+  bool in = true;
+  if (a.bc == BC_PERIODIC) {
+    g = vidx(a, wrap_index(x, a.nx), wrap_index(y, a.ny), wrap_index(z, a.nz));
+  } else {
+    in = x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz;
+    g = vidx(a, clamp_index(x, a.nx), clamp_index(y, a.ny), clamp_index(z, a.nz));
+  }
+  cp_async4(du, a.u + g, in ? 4 : 0);
+  cp_async4(dk, a.k + g, 4);
+}
+
+__global__ void __launch_bounds__(256) vol_ring_kernel(const VolArgs a) {
+  extern __shared__ __align__(16) float ring[];
+  const int lane = threadIdx.x, ty = threadIdx.y, BY = blockDim.y;
+  const int SF = vring_slot_floats(BY);
+  const int KO = (BY + 2) * 128, SO = 2 * (BY + 2) * 128, HO = (3 * BY + 4) * 128;
+  const int xt = blockIdx.x * 128, x0 = xt + 4 * lane;
+  const int y = blockIdx.y * BY + ty;
+  const int z0 = blockIdx.z * a.pz, z1 = min(a.nz, z0 + a.pz);
+  if (z0 >= z1) return;  // uniform over the CTA
+  const bool store = y < a.ny && x0 < a.nx;
+  const bool kghost = a.bc != BC_PERIODIC && x0 >= a.nx;  // ghost columns take kappa of column nx-1
+  const int xh = lane == 0 ? xt - 1 : xt + 128;
+  const int side = lane == 0 ? 0 : 1;
+
+  // issue the copies of plane p into its slot (this thread's share)
+  auto issue = [&](int p) {
+    float* sl = ring + (size_t)(p & (VR - 1)) * SF;
+    ring_row(a, x0, y, p, sl + (ty + 1) * 128 + 4 * lane, sl + KO + (ty + 1) * 128 + 4 * lane,
+             sl + SO + ty * 128 + 4 * lane);
+    if (ty == 0) ring_row(a, x0, y - 1, p, sl + 4 * lane, sl + KO + 4 * lane, nullptr);
+    if (ty == BY - 1)
+      ring_row(a, x0, y + 1, p, sl + (BY + 1) * 128 + 4 * lane, sl + KO + (BY + 1) * 128 + 4 * lane, nullptr);
+    if (lane == 0 || lane == 31) ring_cell(a, xh, y, p, sl + HO + 2 * ty + side, sl + HO + 2 * BY + 2 * ty + side);
+  };
+  for (int p = z0 - 1; p <= z0 + VR - 3; ++p) {
+    if (p <= z1) issue(p);
+    cp_async_commit();
+  }
+  const float dt = a.dt, hdt = a.hdt;
+  for (int z = z0; z < z1; ++z) {
+    cp_async_wait<VR - 4>();  // this thread's copies of planes <= z + 1 have landed
+    __syncthreads();
+    if (z + VR - 2 <= z1) issue(z + VR - 2);
+    cp_async_commit();
+    const float* pm = ring + (size_t)((z - 1) & (VR - 1)) * SF;
+    const float* pc = ring + (size_t)(z & (VR - 1)) * SF;
+    const float* pp = ring + (size_t)((z + 1) & (VR - 1)) * SF;
+    const int r = (ty + 1) * 128 + 4 * lane;
+    const float4 uc = *reinterpret_cast<const float4*>(pc + r);
+    float4 kc = *reinterpret_cast<const float4*>(pc + KO + r);
+    if (kghost) kc = make_float4(kc.w, kc.w, kc.w, kc.w);
+    float uWl = __shfl_up_sync(CPB_FULL_MASK, uc.w, 1), kWl = __shfl_up_sync(CPB_FULL_MASK, kc.w, 1);
+    float uEl = __shfl_down_sync(CPB_FULL_MASK, uc.x, 1), kEl = __shfl_down_sync(CPB_FULL_MASK, kc.x, 1);
+    if (lane == 0 || lane == 31) {
+      const float hu = pc[HO + 2 * ty + side], hk = pc[HO + 2 * BY + 2 * ty + side];
+      if (lane == 0) {
+        uWl = hu;
+        kWl = hk;
+      } else {
+        uEl = hu;
+        kEl = hk;
+      }
+    }
+    if (store) {
+      const float4 uS = *reinterpret_cast<const float4*>(pc + r - 128);
+      const float4 uN = *reinterpret_cast<const float4*>(pc + r + 128);
+      const float4 kS = *reinterpret_cast<const float4*>(pc + KO + r - 128);
+      const float4 kN = *reinterpret_cast<const float4*>(pc + KO + r + 128);
+      const float4 um = *reinterpret_cast<const float4*>(pm + r);
+      const float4 km = *reinterpret_cast<const float4*>(pm + KO + r);
+      const float4 up = *reinterpret_cast<const float4*>(pp + r);
+      const float4 kp = *reinterpret_cast<const float4*>(pp + KO + r);
+      const float4 sc = *reinterpret_cast<const float4*>(pc + SO + ty * 128 + 4 * lane);
+      float4 o;
+      o.x = update7(uc.x, uWl, uc.y, uS.x, uN.x, um.x, up.x, kc.x, kWl, kc.y, kS.x, kN.x, km.x, kp.x, sc.x,
+                    dt, hdt);
+      o.y = update7(uc.y, uc.x, uc.z, uS.y, uN.y, um.y, up.y, kc.y, kc.x, kc.z, kS.y, kN.y, km.y, kp.y, sc.y,
+                    dt, hdt);
+      o.z = update7(uc.z, uc.y, uc.w, uS.z, uN.z, um.z, up.z, kc.z, kc.y, kc.w, kS.z, kN.z, km.z, kp.z, sc.z,
+                    dt, hdt);
+      o.w = update7(uc.w, uc.z, uEl, uS.w, uN.w, um.w, up.w, kc.w, kc.z, kEl, kS.w, kN.w, km.w, kp.w, sc.w,
+                    dt, hdt);
+      *reinterpret_cast<float4*>(a.uo + vidx(a, x0, y, z)) = o;
+    }
+  }
+  cp_async_wait<0>();  // no copy may target this CTA's shared memory after it exits
+}
+
 }  // namespace
 
-size_t vol_smem_bytes(int by) { return (size_t)4 * (by + 2) * 32 * sizeof(float4); }
+size_t vol_smem_bytes(int by) {
+  const size_t reg = (size_t)4 * (by + 2) * 32 * sizeof(float4);       // register kernel
+  const size_t rng = (size_t)VR * vring_slot_floats(by) * sizeof(float);  // plane-ring kernel
+  return reg > rng ? reg : rng;
+}
+
+namespace {
+unsigned g_vol_attr_done;  // devices on which the ring kernel's shared-memory opt-in was set
+cudaError_t vol_ring_optin(size_t shm) {
+  if (shm <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && (g_vol_attr_done & (1u << dev))) return cudaSuccess;
+  e = cudaFuncSetAttribute((const void*)vol_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)vol_smem_bytes(8));
+  if (e == cudaSuccess && dev < 32) g_vol_attr_done |= 1u << dev;
+  return e;
+}
+}  // namespace
 
 cudaError_t launch_vol_f32(const float* u_in, float* u_out, const float* kappa, const float* src, int nx,
                            int ny, int nz, float dt, int bc, int vec, dim3 grid, int by, cudaStream_t s) {
@@ -240,8 +406,16 @@ cudaError_t launch_vol_f32(const float* u_in, float* u_out, const float* kappa, 
   a.bc = bc;
   a.vec = vec;
   a.pz = (nz + (int)grid.z - 1) / (int)grid.z;
-  (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
-  vol_kernel<<<grid, dim3(32, by, 1), vol_smem_bytes(by), s>>>(a);
+  if (vec) {
+    const size_t shm = (size_t)VR * vring_slot_floats(by) * sizeof(float);
+    cudaError_t e = vol_ring_optin(shm);
+    if (e != cudaSuccess) return e;
+    (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
+    vol_ring_kernel<<<grid, dim3(32, by, 1), shm, s>>>(a);
+  } else {
+    (void)cudaGetLastError();
+    vol_kernel<<<grid, dim3(32, by, 1), (size_t)4 * (by + 2) * 32 * sizeof(float4), s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ def run3(L, g, dev, block=(0, 0, 0), zc=None, scratch=True, steps=None, src=True
     else:
         by = block[1]
         grid = ((g.nx + 127) // 128, (g.ny + by - 1) // by, zc)
-        shm = 2048 * (by + 2)
+        shm = L.cpb_stencil3d_shared_bytes(by)
     L.cpb_stencil3d_launch(u_in, out, k, s, g.nx, g.ny, g.nz, steps, float(g.dt), g.bc, grid, block, shm,
                            scratch=scr)
     torch.cuda.synchronize()
@@ -82,7 +82,7 @@ def test_vol_misaligned_takes_scalar_path(dev):
     k.copy_(torch.from_numpy(g.kappa.reshape(-1)))
     s.copy_(torch.from_numpy(g.src.reshape(-1)))
     L.cpb_stencil3d_launch(u, out, k, s, g.nx, g.ny, g.nz, g.steps, float(g.dt), D, (2, 2, 2), (32, 8, 1),
-                           2048 * 10)
+                           L.cpb_stencil3d_shared_bytes(8))
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy().reshape(g.u.shape), ref)
 
@@ -116,7 +116,8 @@ def test_vol_error_codes(dev):
             L.cpb_stencil3d_launch(u, uo, k, None, nx, ny, nz, steps, dt, D, grid, block, shm)
         return e.value.status
 
-    shm = 2048 * 10
+    shm = L.cpb_stencil3d_shared_bytes(8)
+    assert shm > 0 and L.cpb_stencil3d_shared_bytes(9) == 0 and L.cpb_stencil3d_shared_bytes(0) == 0
     assert call((1, 1, 1), (33, 8, 1), shm) == cpb.CPB_ERR_UNSUPPORTED_CONFIG
     assert call((1, 1, 1), (32, 9, 1), 1 << 16) == cpb.CPB_ERR_UNSUPPORTED_CONFIG
     assert call((2, 1, 1), (32, 8, 1), shm) == cpb.CPB_ERR_INVALID_VALUE     # grid.x != ceil(nx/128)
