@@ -216,8 +216,8 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
  * planes stream through an 8-slot shared-memory ring filled by asynchronous
  * copies several planes ahead; otherwise each thread loads the next plane
  * into registers.  block = {0,0,0} selects by = 8 and z-chunks of about
- * 16 planes.  Validation and errors as
- * for cpb_stencil_launch; asynchronous on `stream`. */
+ * 32 planes.  Validation and errors as for cpb_stencil_launch; asynchronous
+ * on `stream`. */
 size_t cpb_stencil3d_shared_bytes(int by); /* 0 if by is outside 1..8 */
 cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
                                 int ny, int nz, int steps, float dt, cpb_boundary bc, cpb_dim3 grid,
