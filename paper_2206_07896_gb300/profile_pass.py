@@ -1,16 +1,45 @@
 """One full-depth pass of the tuned stream kernel per tuning, for profilers.
 
     python -m paper_2206_07896_gb300.profile_pass N K:chunk:wpb:variant:stages [...]
+    python -m paper_2206_07896_gb300.profile_pass vol N by:zchunks [...]
 
 Builds the N x N periodic FP32 workload (the seeded generator of the scale
 runs), then launches, for each tuning given, ONE pass of depth K through
 cpb_stencil_launch_tuned, so a profiler capturing `-k regex:stream -c <count>`
-sees exactly one launch per tuning.  Prints one line and exits 0.
+sees exactly one launch per tuning.  With `vol`: the N^3 volume workload and
+ONE step of cpb_stencil3d_launch per geometry (block 32 x by, grid.z =
+zchunks).  Prints one line and exits 0.
 """
 import sys
 
 
+def main_vol(argv):
+    import torch
+
+    import workloads as W
+    from . import lib
+
+    n = int(argv[0]) if argv and ":" not in argv[0] else 256
+    specs = [a for a in argv if ":" in a] or ["8:16"]
+    L = lib(True)
+    g = W.volume(n=n, steps=1)
+    dev = torch.device("cuda")
+    u = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy(g.src).to(dev)
+    out = torch.empty_like(u)
+    for sp in specs:
+        by, zc = (int(x) for x in sp.split(":"))
+        L.cpb_stencil3d_launch(u, out, k, s, n, n, n, 1, float(g.dt), g.bc, ((n + 127) // 128, (n + by - 1) // by, zc),
+                               (32, by, 1), L.cpb_stencil3d_shared_bytes(by))
+    torch.cuda.synchronize()
+    print("profile_pass vol", n, specs, "ok")
+    return 0
+
+
 def main(argv):
+    if argv and argv[0] == "vol":
+        return main_vol(argv[1:])
     import torch
 
     import workloads as W
