@@ -131,9 +131,29 @@ cpb_status cpb_stencil_launch_tuned(void* u_in, void* u_out, const void* kappa, 
                                     cpb_dtype dtype, const cpb_tuning* tuning, void* scratch,
                                     cpb_stream_t stream);
 
-/* Tuning cache (process-wide, keyed by nx, ny, dtype, bc). */
+/* Tuning cache (process-wide, keyed by nx, ny, dtype, bc).  cpb_get_tuning
+ * returns the cached tuning or the built-in default; cpb_lookup_tuning sets
+ * *found to 1 and *t only when a tuning is cached for the key. */
 cpb_status cpb_set_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, const cpb_tuning* t);
 cpb_status cpb_get_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_tuning* t);
+cpb_status cpb_lookup_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_tuning* t,
+                             int* found);
+
+/* Persistent tuning cache: a tuning is a measurement on one device for one
+ * grid shape, worth keeping between processes (autotuning a large grid takes
+ * seconds).  Text file, one tuning per line:
+ *   cpb-tuning 1 <device> <nx> <ny> <dtype> <bc> <k> <chunk_rows> <warps_per_block> <variant> <stages>
+ * where <device> is the device name with every blank replaced by '_'.
+ * cpb_tuning_save writes every tuning cached in this process under `device`
+ * (NULL: the current device's name), replacing the file (written to a
+ * temporary name, then renamed).  cpb_tuning_load caches every line whose
+ * device equals `device` (NULL: the current device's name) and writes how
+ * many in *loaded (may be NULL); lines of other devices are skipped.  A line
+ * that does not parse or holds an invalid tuning, or a file that cannot be
+ * opened, gives CPB_ERR_INVALID_VALUE (lines before a bad one stay loaded).
+ * With `device` given, neither call touches the GPU. */
+cpb_status cpb_tuning_save(const char* path, const char* device);
+cpb_status cpb_tuning_load(const char* path, const char* device, int* loaded);
 
 /* Time candidate tunings on the caller's buffers (u_a and u_b are
  * clobbered; kappa, src read) for `steps` steps each, store the fastest in the

@@ -88,6 +88,9 @@ _SIGS = {
                                       C.POINTER(cpb_tuning), _vp, _vp]),
     "cpb_set_tuning": (_i, [_i, _i, _i, _i, C.POINTER(cpb_tuning)]),
     "cpb_get_tuning": (_i, [_i, _i, _i, _i, C.POINTER(cpb_tuning)]),
+    "cpb_lookup_tuning": (_i, [_i, _i, _i, _i, C.POINTER(cpb_tuning), C.POINTER(_i)]),
+    "cpb_tuning_save": (_i, [C.c_char_p, C.c_char_p]),
+    "cpb_tuning_load": (_i, [C.c_char_p, C.c_char_p, C.POINTER(_i)]),
     "cpb_autotune": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, C.POINTER(cpb_tuning)]),
     "cpb_device_status": (_i, [C.POINTER(_i)]),
     "cpb_debug_set": (_i, [_i, _i]),
@@ -221,6 +224,20 @@ class Library:
         t = cpb_tuning()
         self._call("cpb_get_tuning", nx, ny, dtype, bc, C.byref(t))
         return t.as_dict()
+
+    def cpb_lookup_tuning(self, nx, ny, dtype, bc):
+        """The cached tuning (dict) for the key, or None."""
+        t, found = cpb_tuning(), _i()
+        self._call("cpb_lookup_tuning", nx, ny, dtype, bc, C.byref(t), C.byref(found))
+        return t.as_dict() if found.value else None
+
+    def cpb_tuning_save(self, path, device=None):
+        self._call("cpb_tuning_save", os.fsencode(path), device.encode() if device else None)
+
+    def cpb_tuning_load(self, path, device=None) -> int:
+        n = _i()
+        self._call("cpb_tuning_load", os.fsencode(path), device.encode() if device else None, C.byref(n))
+        return n.value
 
     def cpb_autotune(self, u_a, u_b, kappa, src, nx, ny, steps, dt, bc, dtype, stream=None) -> dict:
         t = cpb_tuning()

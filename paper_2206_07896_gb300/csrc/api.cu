@@ -15,6 +15,8 @@
 #include <tuple>
 #include <vector>
 
+#include <unistd.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -257,6 +259,32 @@ cpb_status enqueue_tile(const Fields& f, int nx, int ny, int steps, float dt, cp
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+#define CPB_TRY_STATUS(expr)             \
+  do {                                   \
+    cpb_status _s = (expr);              \
+    if (_s != CPB_SUCCESS) return _s;    \
+  } while (0)
+
+// Device tag of the tuning file: the given name, or the current device's
+// name, with blanks replaced by '_'.
+cpb_status device_tag(const char* device, std::string* out) {
+  std::string d;
+  if (device) {
+    d = device;
+  } else {
+    int dev = 0;
+    cudaDeviceProp prop;
+    CPB_TRY(cudaGetDevice(&dev));
+    CPB_TRY(cudaGetDeviceProperties(&prop, dev));
+    d = prop.name;
+  }
+  if (d.empty()) return CPB_ERR_INVALID_VALUE;
+  for (char& c : d)
+    if (c == ' ' || c == '\t' || c == '\n') c = '_';
+  *out = d;
+  return CPB_SUCCESS;
+}
+
 }  // namespace
 
 struct cpb_graph_s {
@@ -389,6 +417,83 @@ cpb_status cpb_get_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_
   if (!t || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
   *t = lookup_tuning(nx, ny, dtype, bc);
   return CPB_SUCCESS;
+}
+
+cpb_status cpb_lookup_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_tuning* t,
+                             int* found) {
+  if (!t || !found || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  auto it = g_tune.find(TuneKey(nx, ny, (int)dtype, (int)bc));
+  *found = it != g_tune.end() ? 1 : 0;
+  if (*found) *t = it->second;
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_tuning_save(const char* path, const char* device) {
+  if (!path) return CPB_ERR_INVALID_VALUE;
+  std::string dev;
+  CPB_TRY_STATUS(device_tag(device, &dev));
+  const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) {
+    g_last_error = "cannot write " + tmp;
+    return CPB_ERR_INVALID_VALUE;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (const auto& kv : g_tune) {
+      const cpb_tuning& t = kv.second;
+      std::fprintf(f, "cpb-tuning 1 %s %d %d %d %d %d %d %d %d %d\n", dev.c_str(), std::get<0>(kv.first),
+                   std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first), t.k, t.chunk_rows,
+                   t.warps_per_block, t.variant, t.stages);
+    }
+  }
+  const bool ok = std::fflush(f) == 0;
+  std::fclose(f);
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    g_last_error = std::string("cannot replace ") + path;
+    return CPB_ERR_INVALID_VALUE;
+  }
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_tuning_load(const char* path, const char* device, int* loaded) {
+  if (loaded) *loaded = 0;
+  if (!path) return CPB_ERR_INVALID_VALUE;
+  std::string dev;
+  CPB_TRY_STATUS(device_tag(device, &dev));
+  FILE* f = std::fopen(path, "r");
+  if (!f) {
+    g_last_error = std::string("cannot open ") + path;
+    return CPB_ERR_INVALID_VALUE;
+  }
+  char line[512];
+  int n = 0;
+  cpb_status st = CPB_SUCCESS;
+  while (std::fgets(line, sizeof line, f)) {
+    char name[256];
+    int ver, nx, ny, dt, bc;
+    cpb_tuning t;
+    char tail = 0;
+    const int got = std::sscanf(line, "cpb-tuning %d %255s %d %d %d %d %d %d %d %d %d %c", &ver, name, &nx, &ny,
+                                &dt, &bc, &t.k, &t.chunk_rows, &t.warps_per_block, &t.variant, &t.stages, &tail);
+    if (got != 11 || ver != 1 || nx < 1 || ny < 1 || (dt != CPB_F32 && dt != CPB_BF16_KAHAN) ||
+        (bc != CPB_DIRICHLET0 && bc != CPB_PERIODIC) || !tuning_valid(t)) {
+      g_last_error = std::string("bad tuning line: ") + line;
+      st = CPB_ERR_INVALID_VALUE;
+      break;
+    }
+    if (dev != name) continue;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mutex);
+      g_tune[TuneKey(nx, ny, dt, bc)] = t;
+    }
+    ++n;
+  }
+  std::fclose(f);
+  if (loaded) *loaded = n;
+  return st;
 }
 
 cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src, int nx, int ny,

@@ -300,6 +300,29 @@ def test_graph_replays_the_run(dev, exact):
         exact.cpb_graph_destroy(gr)
 
 
+@pytest.mark.parametrize("dtype", [cpb.CPB_F32, cpb.CPB_BF16_KAHAN])
+@pytest.mark.parametrize("split", [1, 13, 37])
+def test_resume_from_saved_state(dev, exact, dtype, split):
+    # Checkpoint / resume: the state is u alone (the (hi, cmp) words for
+    # BF16-Kahan), so stopping after `split` steps and resuming from the stored
+    # state gives the same bits as one run, whatever the pass schedules.
+    g = W.random_grid(31, 520, 77, 50, P)
+    t = {"k": 8, "chunk_rows": 24, "warps_per_block": 2, "variant": 1, "stages": 2}
+    if dtype == cpb.CPB_F32:
+        fields = (to_dev(g.u, dev), to_dev(g.kappa, dev), to_dev(g.src, dev))
+    else:
+        fields = (to_dev(oracle.bf16k_pack(g.u).view(np.int32), dev),
+                  to_dev(oracle.bf16_round(g.kappa).view(np.int16), dev),
+                  to_dev(oracle.bf16_round(g.src).view(np.int16), dev))
+    whole = run_tuned(exact, g, dev, t, steps=g.steps, dtype=dtype, fields=fields)
+    first = run_tuned(exact, g, dev, t, steps=split, dtype=dtype, fields=fields)
+    resumed = (torch.from_numpy(first).to(dev),) + fields[1:]
+    second = run_tuned(exact, g, dev, t, steps=g.steps - split, dtype=dtype, fields=resumed)
+    np.testing.assert_array_equal(second.view(np.uint32), whole.view(np.uint32))
+    if dtype == cpb.CPB_F32:
+        np.testing.assert_array_equal(whole, oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, P, "f32"))
+
+
 def test_tuning_cache_and_autotune(dev, exact):
     g = W.random_grid(8, 640, 256, 12, P)
     ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, P, "f32")
