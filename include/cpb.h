@@ -131,17 +131,23 @@ cpb_status cpb_stencil_launch_tuned(void* u_in, void* u_out, const void* kappa, 
                                     cpb_dtype dtype, const cpb_tuning* tuning, void* scratch,
                                     cpb_stream_t stream);
 
-/* Tuning cache (process-wide, keyed by nx, ny, dtype, bc).  cpb_get_tuning
- * returns the cached tuning or the built-in default; cpb_lookup_tuning sets
- * *found to 1 and *t only when a tuning is cached for the key. */
+/* Tuning cache (process-wide, keyed by nx, ny, dtype, bc).  The paper's
+ * nearest counterpart is the per-kernel block_per_fetch its runtime sets
+ * (Sec. IV "Runtime Optimizations"); here a tuning fixes the temporal depth
+ * and the work shape of the tuned path.  cpb_get_tuning returns the cached
+ * tuning or the built-in default; cpb_lookup_tuning sets *found to 1 and *t
+ * only when a tuning is cached for the key.  Errors: null pointers or
+ * nx, ny < 1 give CPB_ERR_INVALID_VALUE; an invalid tuning given to
+ * cpb_set_tuning gives CPB_ERR_INVALID_VALUE. */
 cpb_status cpb_set_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, const cpb_tuning* t);
 cpb_status cpb_get_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_tuning* t);
 cpb_status cpb_lookup_tuning(int nx, int ny, cpb_dtype dtype, cpb_boundary bc, cpb_tuning* t,
                              int* found);
 
-/* Persistent tuning cache: a tuning is a measurement on one device for one
- * grid shape, worth keeping between processes (autotuning a large grid takes
- * seconds).  Text file, one tuning per line:
+/* Persistent tuning cache (no counterpart in the paper): a tuning is a
+ * measurement on one device for one grid shape, worth keeping between
+ * processes (autotuning a large grid takes seconds).  Text file, one tuning
+ * per line:
  *   cpb-tuning 1 <device> <nx> <ny> <dtype> <bc> <k> <chunk_rows> <warps_per_block> <variant> <stages>
  * where <device> is the device name with every blank replaced by '_'.
  * cpb_tuning_save writes every tuning cached in this process under `device`
@@ -157,7 +163,12 @@ cpb_status cpb_tuning_load(const char* path, const char* device, int* loaded);
 
 /* Time candidate tunings on the caller's buffers (u_a and u_b are
  * clobbered; kappa, src read) for `steps` steps each, store the fastest in the
- * cache and return it in *best.  Synchronises `stream`. */
+ * cache and return it in *best.  Synchronises `stream`.  The paper leaves the
+ * choice of its grain size to heuristics per kernel (Sec. IV "Runtime
+ * Optimizations"); this measures instead.  Candidates: depth 1..6 and 8,
+ * chunk 64..512 rows, 1..4 warps per CTA, both row-load variants, 2..8 ring
+ * stages; each timed once, the best eight again four times.  Arguments are
+ * validated as for cpb_stencil_launch. */
 cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src, int nx, int ny,
                         int steps, float dt, cpb_boundary bc, cpb_dtype dtype, cpb_stream_t stream,
                         cpb_tuning* best);
