@@ -368,11 +368,17 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
                                        cpb.CPB_F32, tuning=None, scratch=scratch[:c], stream=sh)
 
     ms_each = _time(run_each, 1, stream)
+    # kernel launches of the per-grid baseline: passes of depth 4 (scratch given)
+    n_launch_each = int(sum(-(-int(st) // 4) for st in bt.steps))
     return {"workload": f"batch-{bt.ngrids}-grids-32..1024-steps-10..500", "updates": upd,
             "cells": int(cells.sum()), "n_large": n_large, "plan": plan,
             "grain_sweep_ms": {f"grain{g}_threads{t}": v for (g, t), v in sweep.items()},
             "batched": {"gcells": upd / ms_b / 1e6, "ms": ms_b, "status": status},
-            "one_grid_at_a_time": {"gcells": upd / ms_each / 1e6, "ms": ms_each},
+            "one_grid_at_a_time": {"gcells": upd / ms_each / 1e6, "ms": ms_each,
+                                   "launches": n_launch_each,
+                                   "note": "one cpb_stencil_launch_tuned call per grid from Python at "
+                                           "the default depth 4, i.e. launch-bound: the cost the "
+                                           "single persistent launch removes"},
             "speedup_batched_vs_per_grid": ms_each / ms_b}
 
 
