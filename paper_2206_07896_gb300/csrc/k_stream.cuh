@@ -236,11 +236,12 @@ __device__ __forceinline__ float2 madd2(float2 h, float2 acc, float2 ds) {
 __device__ __forceinline__ float2 kahan_round2(float2 v, uint2& words) {
   const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
   const float2 hif = __bfloat1622float2(hi);
-  const __nv_bfloat162 cm = __floats2bfloat162_rn(hif.x - v.x, hif.y - v.y);
+  const float2 r = sub2(hif, v);  // hi - v, both components in one packed operation
+  const __nv_bfloat162 cm = __floats2bfloat162_rn(r.x, r.y);
   const float2 cmf = __bfloat1622float2(cm);
   const unsigned hb = *reinterpret_cast<const unsigned*>(&hi), cb = *reinterpret_cast<const unsigned*>(&cm);
   words = make_uint2(__byte_perm(hb, cb, 0x5410), __byte_perm(hb, cb, 0x7632));
-  return make_float2(hif.x - cmf.x, hif.y - cmf.y);
+  return sub2(hif, cmf);  // hi - cmp
 }
 
 // The K-level pipeline of one warp strip, in flux form.
