@@ -144,7 +144,7 @@ def strip_warp(u, kappa, src, steps, dt, bc, precision="f32", k=4, chunk=64, war
     strip, 4 cells per lane, k time levels per pass) executed per the paper's
     execution model for kernels with warp-level functions: nested warp / lane
     loops split at every shuffle (Sec. III-B).  fission=False ignores the
-    split at the shuffles (for the test showing it is needed).  k <= 7."""
+    split at the shuffles (for the test showing it is needed).  k <= 8."""
     ny, nx = u.shape
     T, fn = (np.float64, "orc_strip_warp_f64") if precision == "f64" else (np.float32, "orc_strip_warp_f32")
     out = np.empty((ny, nx), T)

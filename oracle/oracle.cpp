@@ -563,8 +563,8 @@ int count_mpmd(void** p) {
 // needed.
 template <class T>
 struct WarpLane {
-  // rings indexed by row mod 3 (levels 0 .. K-1) and row mod (K + 2) (inputs)
-  T lev[8][3][4];
+  // rings indexed by row mod 3 (levels 0 .. K) and row mod (K + 2) (inputs)
+  T lev[9][3][4];
   T kap[10][6];  // kW, k0..k3, kE of a row
   T src[10][4];
 };
@@ -615,7 +615,7 @@ int strip_warp_mpmd(void** p) {
     // Exchange slots start as NaN so a read of an unwritten slot shows.
     for (int l = 0; l < 32; ++l) x_a[l] = x_b[l] = std::numeric_limits<T>::quiet_NaN();
     for (int l = 0; l < 32; ++l)
-      for (int t = 0; t < 8; ++t)
+      for (int t = 0; t < 9; ++t)
         for (int q = 0; q < 3; ++q)
           for (int e = 0; e < 4; ++e) lanes[l].lev[t][q][e] = T(0);
 
@@ -696,7 +696,7 @@ int strip_warp_mpmd(void** p) {
 template <class T>
 int run_strip_warp(const T* u0, const T* k, const T* s, int nx, int ny, int steps, T dt, int bc, int K,
                    int chunk, int W, int pool, int fission, T* out) {
-  if (K < 1 || K > 7 || chunk < 1 || W < 1 || W > 32) return 1;
+  if (K < 1 || K > 8 || chunk < 1 || W < 1 || W > 32) return 1;
   size_t n = (size_t)nx * ny;
   T hdt = T(0.5) * dt;
   std::vector<T> a(u0, u0 + n), b(n);
@@ -1165,7 +1165,7 @@ int orc_adjoint_f64(const double* u0, const double* k, const double* s, const do
   return 0;
 }
 
-// The warp-level strip kernel (K <= 7: level rings hold 8 levels).
+// The warp-level strip kernel (K <= 8, the depths of the GPU path).
 int orc_strip_warp_f32(const float* u0, const float* k, const float* s, int nx, int ny, int steps,
                        float dt, int bc, int K, int chunk, int warps, int pool, int fission, float* out) {
   if (nx < 1 || ny < 1 || steps < 0) return 1;

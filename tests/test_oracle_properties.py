@@ -35,7 +35,7 @@ def test_fission_equals_direct(nx, ny, steps, bc, bx, by, pool, grain, seed):
 
 @settings(max_examples=40, deadline=None)
 @given(nx=st.integers(1, 300), ny=st.integers(1, 30), steps=st.integers(0, 9), bc=bcs,
-       k=st.integers(1, 7), chunk=st.integers(1, 40), warps=st.integers(1, 4), pool=st.integers(1, 4),
+       k=st.integers(1, 8), chunk=st.integers(1, 40), warps=st.integers(1, 4), pool=st.integers(1, 4),
        seed=st.integers(0, 2 ** 16))
 def test_strip_warp_equals_direct(nx, ny, steps, bc, k, chunk, warps, pool, seed):
     g = W.random_grid(seed, nx, ny, steps, bc)
