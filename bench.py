@@ -372,7 +372,7 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     n_launch_each = int(sum(-(-int(st) // 4) for st in bt.steps))
     return {"workload": f"batch-{bt.ngrids}-grids-32..1024-steps-10..500", "updates": upd,
             "cells": int(cells.sum()), "n_large": n_large, "plan": plan,
-            "grain_sweep_ms": {f"grain{g}_threads{t}": v for (g, t), v in sweep.items()},
+            "grain_sweep_ms": {f"depth{d}_grain{g}_threads{t}": v for (d, g, t), v in sweep.items()},
             "batched": {"gcells": upd / ms_b / 1e6, "ms": ms_b, "status": status},
             "one_grid_at_a_time": {"gcells": upd / ms_each / 1e6, "ms": ms_each,
                                    "launches": n_launch_each,

@@ -261,7 +261,9 @@ cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, cons
  * Sec. IV "Fetch task queue" and "Runtime Optimizations").  Grids with at
  * least team_cells cells run on a whole CTA, smaller ones on one warp.
  * Each grid's result is written to its u_out; its u_in is clobbered (used as
- * the ping-pong buffer).  Every grid advances at temporal depth 4.  Grids
+ * the ping-pong buffer).  Every grid advances plan->depth (4 or 8) time
+ * steps per pass; at depth 8 the row loop takes rows in pairs, as in the
+ * single-grid kernel.  Grids
  * whose u_in, u_out, kappa and src are 16-byte aligned with nx % 4 == 0 and
  * nx >= 128 stream their rows through a per-warp TMA ring (bounded waits, as
  * in the variant-1 single-grid kernel); the others load rows with ordinary
@@ -293,8 +295,9 @@ typedef struct {
 typedef struct {
   int grain;      /* grids per queue fetch (>= 1) */
   int blocks;     /* persistent CTAs (<= 0: one wave filling the GPU) */
-  int threads;    /* threads per CTA, a multiple of 32, <= 384 */
+  int threads;    /* threads per CTA, a multiple of 32, <= 384 at depth 4, <= 256 at depth 8 */
   int team_cells; /* grids with nx*ny >= team_cells run on a whole CTA */
+  int depth;      /* time steps per pass over a grid: 4 or 8 */
 } cpb_batch_plan;
 
 cpb_status cpb_batch_plan_default(cpb_batch_plan* plan);
@@ -312,19 +315,22 @@ cpb_status cpb_batch_status(const int* d_work, int* status, cpb_stream_t stream)
  * coarse-grained fetching"): more grids per atomic fetch means fewer fetches
  * but a coarser balance of work over the resident CTAs, so the best grain
  * depends on the batch.  The call times the batch once for every candidate
- * (grain, threads) in CPB_BATCH_TUNE_GRAINS x CPB_BATCH_TUNE_THREADS, grain
- * major, with plan->team_cells and one wave of CTAs, re-times the three
- * fastest twice and writes the fastest plan to *plan (blocks = 0).
- * ms_table (optional, host, CPB_BATCH_TUNE_CANDIDATES floats) receives the
- * single-run time of every candidate in milliseconds (-1 where the launch
- * was rejected).  Arguments as for cpb_stencil_batched, with d_order built
+ * (depth, grain, threads) in CPB_BATCH_TUNE_DEPTHS x CPB_BATCH_TUNE_GRAINS x
+ * CPB_BATCH_TUNE_THREADS, in that nesting, with plan->team_cells and one
+ * wave of CTAs, re-times the three fastest twice and writes the fastest plan
+ * to *plan (blocks = 0).  ms_table (optional, host,
+ * CPB_BATCH_TUNE_CANDIDATES floats) receives the single-run time of every
+ * candidate in milliseconds (-1 where the plan is not valid, e.g. 384
+ * threads at depth 8, or the launch was rejected).  Arguments as for cpb_stencil_batched, with d_order built
  * for plan->team_cells.  The batch runs several times: every grid's u_in
  * and u_out are overwritten, so tune on copies of the fields.  Synchronises
  * `stream`.  A status word other than CPB_SUCCESS after a run is returned
  * (the plan is then left unchanged). */
+#define CPB_BATCH_TUNE_DEPTHS 2   /* 4, 8 */
 #define CPB_BATCH_TUNE_GRAINS 5   /* 1, 2, 4, 8, 16 */
 #define CPB_BATCH_TUNE_THREADS 3  /* 128, 256, 384 */
-#define CPB_BATCH_TUNE_CANDIDATES (CPB_BATCH_TUNE_GRAINS * CPB_BATCH_TUNE_THREADS)
+#define CPB_BATCH_TUNE_CANDIDATES \
+  (CPB_BATCH_TUNE_DEPTHS * CPB_BATCH_TUNE_GRAINS * CPB_BATCH_TUNE_THREADS)
 cpb_status cpb_batch_autotune(const cpb_grid_desc* d_descs, const int* d_order, int ngrids,
                               int n_large, cpb_dtype dtype, cpb_boundary bc, int* d_work,
                               cpb_stream_t stream, cpb_batch_plan* plan, float* ms_table);

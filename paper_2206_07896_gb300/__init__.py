@@ -52,15 +52,16 @@ class cpb_grid_desc(C.Structure):
                 ("dt", C.c_float)]
 
 
-# Candidates of cpb_batch_autotune (include/cpb.h), grain major.
+# Candidates of cpb_batch_autotune (include/cpb.h): depth, then grain, then threads.
+BATCH_TUNE_DEPTHS = (4, 8)
 BATCH_TUNE_GRAINS = (1, 2, 4, 8, 16)
 BATCH_TUNE_THREADS = (128, 256, 384)
-BATCH_TUNE_CANDIDATES = len(BATCH_TUNE_GRAINS) * len(BATCH_TUNE_THREADS)
+BATCH_TUNE_CANDIDATES = len(BATCH_TUNE_DEPTHS) * len(BATCH_TUNE_GRAINS) * len(BATCH_TUNE_THREADS)
 
 
 class cpb_batch_plan(C.Structure):
     _fields_ = [("grain", C.c_int), ("blocks", C.c_int), ("threads", C.c_int),
-                ("team_cells", C.c_int)]
+                ("team_cells", C.c_int), ("depth", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -312,17 +313,19 @@ class Library:
 
     def cpb_batch_autotune(self, d_descs, d_order, ngrids, n_large, dtype, bc, d_work, plan=None,
                            stream=None):
-        """Returns (best plan dict, {(grain, threads): ms or None}).  Overwrites
-        every grid's u_in and u_out (tune on copies)."""
+        """Returns (best plan dict, {(depth, grain, threads): ms or None}).
+        Overwrites every grid's u_in and u_out (tune on copies)."""
         pl = as_plan(plan if plan is not None else self.cpb_batch_plan_default())
         table = (C.c_float * BATCH_TUNE_CANDIDATES)()
         self._call("cpb_batch_autotune", ptr(d_descs), ptr(d_order), ngrids, n_large, dtype, bc,
                    ptr(d_work), stream_handle(stream), C.byref(pl), table)
         ms = {}
-        for gi, g in enumerate(BATCH_TUNE_GRAINS):
-            for ti, t in enumerate(BATCH_TUNE_THREADS):
-                v = table[gi * len(BATCH_TUNE_THREADS) + ti]
-                ms[(g, t)] = float(v) if v > 0 else None
+        i = 0
+        for d in BATCH_TUNE_DEPTHS:
+            for g in BATCH_TUNE_GRAINS:
+                for t in BATCH_TUNE_THREADS:
+                    ms[(d, g, t)] = float(table[i]) if table[i] > 0 else None
+                    i += 1
         return pl.as_dict(), ms
 
     def cpb_adjoint_workspace_bytes(self, nx, ny, steps, ckpt_every) -> int:
@@ -372,9 +375,11 @@ def as_tuning(t) -> cpb_tuning:
 def as_plan(p) -> cpb_batch_plan:
     if isinstance(p, cpb_batch_plan):
         return p
-    d = {"grain": 1, "blocks": 0, "threads": 384, "team_cells": 65536}
+    d = {"grain": 1, "blocks": 0, "team_cells": 65536, "depth": 4}
     d.update(p)
-    return cpb_batch_plan(int(d["grain"]), int(d["blocks"]), int(d["threads"]), int(d["team_cells"]))
+    d.setdefault("threads", 384 if int(d["depth"]) <= 4 else 256)
+    return cpb_batch_plan(int(d["grain"]), int(d["blocks"]), int(d["threads"]), int(d["team_cells"]),
+                          int(d.get("depth", 4)))
 
 
 _LIBS: dict[bool, Library] = {}

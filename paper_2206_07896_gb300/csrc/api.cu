@@ -667,7 +667,8 @@ cpb_status cpb_batch_plan_default(cpb_batch_plan* plan) {
   if (!plan) return CPB_ERR_INVALID_VALUE;
   plan->grain = 1;
   plan->blocks = 0;
-  plan->threads = batch_threads_max();
+  plan->depth = 4;
+  plan->threads = batch_threads_max(plan->depth);
   // Measured on the 4096-grid set (sides 32..1024): a whole CTA per grid down
   // to 32 x 32 beats one warp per small grid (a long small grid on one warp
   // becomes the critical path): 154 ms at 1024 vs 231 ms at 65536.
@@ -684,8 +685,8 @@ bool host_desc_ok(const cpb_grid_desc& g) {
 }
 
 bool plan_ok(const cpb_batch_plan& p) {
-  return p.grain >= 1 && p.threads >= 32 && p.threads % 32 == 0 && p.threads <= batch_threads_max() &&
-         p.team_cells >= 1;
+  return p.grain >= 1 && p.threads >= 32 && p.threads % 32 == 0 && batch_threads_max(p.depth) > 0 &&
+         p.threads <= batch_threads_max(p.depth) && p.team_cells >= 1;
 }
 }  // namespace
 
@@ -729,11 +730,11 @@ cpb_status cpb_stencil_batched(const cpb_grid_desc* d_descs, const int* d_order,
   int blocks = p.blocks;
   if (blocks <= 0) {
     int per_sm = 0;
-    CPB_TRY(batch_blocks_per_sm(p.threads, &per_sm));
+    CPB_TRY(batch_blocks_per_sm(p.depth, p.threads, &per_sm));
     blocks = std::max(1, per_sm) * device_sm_count();
   }
   const BatchDebug dbg{g_wait_limit, g_inject_on, g_inject_row};
-  return from_cuda(launch_batch(d_descs, d_order, ngrids, n_large, (int)bc, p.grain, blocks, p.threads,
+  return from_cuda(launch_batch(p.depth, d_descs, d_order, ngrids, n_large, (int)bc, p.grain, blocks, p.threads,
                                 dbg, d_work, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -751,6 +752,7 @@ cpb_status cpb_batch_autotune(const cpb_grid_desc* d_descs, const int* d_order, 
                               int n_large, cpb_dtype dtype, cpb_boundary bc, int* d_work,
                               cpb_stream_t stream, cpb_batch_plan* plan, float* ms_table) {
   if (!plan || !plan_ok(*plan)) return CPB_ERR_INVALID_VALUE;
+  static const int depths[CPB_BATCH_TUNE_DEPTHS] = {4, 8};
   static const int grains[CPB_BATCH_TUNE_GRAINS] = {1, 2, 4, 8, 16};
   static const int threads[CPB_BATCH_TUNE_THREADS] = {128, 256, 384};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -783,14 +785,17 @@ cpb_status cpb_batch_autotune(const cpb_grid_desc* d_descs, const int* d_order, 
   cpb_batch_plan p = *plan;
   p.blocks = 0;
   time_plan(p, 1);  // warm-up (first launch sets the shared-memory opt-in)
-  for (int gi = 0; gi < CPB_BATCH_TUNE_GRAINS; ++gi)
-    for (int ti = 0; ti < CPB_BATCH_TUNE_THREADS; ++ti) {
-      p.grain = grains[gi];
-      p.threads = threads[ti];
-      const float ms = result == CPB_SUCCESS ? time_plan(p, 1) : -1.0f;
-      if (ms_table) ms_table[gi * CPB_BATCH_TUNE_THREADS + ti] = ms;
-      if (ms > 0.0f) timed.push_back({ms, p});
-    }
+  for (int di = 0; di < CPB_BATCH_TUNE_DEPTHS; ++di)
+    for (int gi = 0; gi < CPB_BATCH_TUNE_GRAINS; ++gi)
+      for (int ti = 0; ti < CPB_BATCH_TUNE_THREADS; ++ti) {
+        p.depth = depths[di];
+        p.grain = grains[gi];
+        p.threads = threads[ti];
+        // a CTA size the depth cannot run is skipped (-1 in the table)
+        const float ms = (result == CPB_SUCCESS && plan_ok(p)) ? time_plan(p, 1) : -1.0f;
+        if (ms_table) ms_table[(di * CPB_BATCH_TUNE_GRAINS + gi) * CPB_BATCH_TUNE_THREADS + ti] = ms;
+        if (ms > 0.0f) timed.push_back({ms, p});
+      }
   std::sort(timed.begin(), timed.end(),
             [](const std::pair<float, cpb_batch_plan>& a, const std::pair<float, cpb_batch_plan>& b) {
               return a.first < b.first;

@@ -74,9 +74,10 @@ cudaError_t launch_bf16k_unpack(const uint32_t* st, float* u, long long n, cudaS
 #include "../../include/cpb.h"
 namespace cpb {
 // Batched persistent launch (k_batch.cu).
-int batch_threads_max();
-int batch_depth();
-cudaError_t batch_blocks_per_sm(int threads, int* out);
+// Largest CTA of the batched kernel at temporal depth `depth` (4 or 8; 0 for
+// any other depth).
+int batch_threads_max(int depth);
+cudaError_t batch_blocks_per_sm(int depth, int threads, int* out);
 // Bounded-wait limit of the TMA row ring and the test-only missing-bytes
 // injection (see StreamPass), passed to the batched kernel by value.
 struct BatchDebug {
@@ -84,7 +85,7 @@ struct BatchDebug {
   int inject_on;
   int inject_row;
 };
-cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
+cudaError_t launch_batch(int depth, const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
                          int grain, int blocks, int threads, const BatchDebug& dbg, int* work,
                          cudaStream_t s);
 }  // namespace cpb

@@ -23,9 +23,15 @@
 namespace cpb {
 namespace {
 
-constexpr int BATCH_K = 4;
-constexpr int BATCH_MAX_THREADS = 384;
 constexpr int BATCH_STAGES = 2;  // TMA ring slots per warp
+
+// Temporal depths the batched kernel is built for, and the largest CTA of
+// each: one CTA per SM, and the registers of depth 8 (rows in pairs) allow
+// at most 256 threads.
+template <int K>
+struct BatchDepth {
+  static constexpr int MAX_THREADS = K <= 4 ? 384 : 256;
+};
 
 // Depth of pass i of a grid with S steps at depth K, with the pass count made
 // odd (split the last pass, or, if it has depth 1, the one before it).
@@ -86,9 +92,9 @@ __device__ __forceinline__ void team_sync() {
 // Run all steps of one grid with a team: the whole CTA (CTA = true) or one warp.
 // sm: this warp's row ring, mbarriers and face ring; tma_ok: the warp's ring
 // is usable (cleared for the rest of the launch if a bounded wait expired).
-template <bool CTA>
+template <int K, bool CTA>
 __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int lane, int* status,
-                         const BulkSmem<BATCH_K, false>& sm, bool& tma_ok, const BatchDebug& dbg) {
+                         const BulkSmem<K, false>& sm, bool& tma_ok, const BatchDebug& dbg) {
   if (!desc_ok(g)) {
     if (lane == 0 && wib == 0) atomicExch(status, (int)CPB_ERR_INVALID_VALUE);
     return;
@@ -102,7 +108,7 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
     team_sync<CTA>();
     return;
   }
-  constexpr int HALO = (BATCH_K + 3) & ~3;
+  constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   StreamArgs a;
   a.kappa = g.kappa;
@@ -123,22 +129,22 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
   // Rows through the TMA ring when the grid allows it (see bulk_eligible in
   // api.cu); otherwise each lane loads its row slices itself.
   const bool bulk = a.vec && nx >= 128;
-  const int P = npasses(S, BATCH_K);
+  const int P = npasses(S, K);
   const void* src_buf = g.u_in;
   for (int i = 0; i < P; ++i) {
     void* dst = ((P - 1 - i) % 2 == 0) ? g.u_out : g.u_in;
     a.u_in = src_buf;
     a.u_out = dst;
-    a.depth = pass_depth(i, S, BATCH_K);
+    a.depth = pass_depth(i, S, K);
     a.chunk_rows = team_chunk_rows(ny, a.n_strips, nw, a.depth);
     a.n_items = a.n_strips * ((ny + a.chunk_rows - 1) / a.chunk_rows);
     for (int it = wib; it < a.n_items; it += nw) {
       if (bulk && tma_ok) {
-        tma_ok = bulk_item<BATCH_K, false, false>(a, it, lane, sm.ring, sm.bars, sm.face, status);
+        tma_ok = bulk_item<K, false, false>(a, it, lane, sm.ring, sm.bars, sm.face, status);
         if (!tma_ok)  // a wait expired (status set): redo this item without the ring
-          stream_item<BATCH_K, false, true>(a, it, lane, sm.face);
+          stream_item<K, false, true>(a, it, lane, sm.face);
       } else {
-        stream_item<BATCH_K, false, true>(a, it, lane, sm.face);
+        stream_item<K, false, true>(a, it, lane, sm.face);
       }
     }
     // This pass's ordinary stores must be visible to the next pass's bulk
@@ -149,14 +155,15 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
   }
 }
 
-__global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
+template <int K>
+__global__ void __launch_bounds__(BatchDepth<K>::MAX_THREADS, 1)
     batch_kernel(const cpb_grid_desc* __restrict__ descs, const int* __restrict__ order, int ngrids,
                  int n_large, int bc, int grain, BatchDebug dbg, int* work) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ int s_first;
   extern __shared__ __align__(128) unsigned char smem[];
   // this warp's row ring, mbarriers and ring of per-row face terms (k_stream.cuh)
-  const BulkSmem<BATCH_K, false> sm(smem, wib, nw, BATCH_STAGES);
+  const BulkSmem<K, false> sm(smem, wib, nw, BATCH_STAGES);
   bool tma_ok = true;
   // Phase 1: large grids, one CTA per grid, fetched `grain` at a time.
   for (;;) {
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
     const int last = min(first + grain, n_large);
     for (int q = first; q < last; ++q) {
       const cpb_grid_desc g = descs[order[q]];
-      run_grid<true>(g, bc, wib, nw, lane, &work[2], sm, tma_ok, dbg);
+      run_grid<K, true>(g, bc, wib, nw, lane, &work[2], sm, tma_ok, dbg);
     }
   }
   // Phase 2: small grids, one warp per grid.
@@ -181,37 +188,48 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 1)
     const int last = min(first + grain, n_small);
     for (int q = first; q < last; ++q) {
       const cpb_grid_desc g = descs[order[n_large + q]];
-      run_grid<false>(g, bc, 0, 1, lane, &work[2], sm, tma_ok, dbg);
+      run_grid<K, false>(g, bc, 0, 1, lane, &work[2], sm, tma_ok, dbg);
     }
   }
 }
 
 }  // namespace
 
-int batch_threads_max() { return BATCH_MAX_THREADS; }
-int batch_depth() { return BATCH_K; }
-
-namespace {
-unsigned g_batch_attr_done;
-size_t batch_smem(int threads) { return stream_smem_bytes(false, BATCH_K, threads / 32, 1, BATCH_STAGES); }
-}  // namespace
-
-cudaError_t batch_blocks_per_sm(int threads, int* out) {
-  cudaError_t e = ensure_smem_optin((const void*)batch_kernel, g_batch_attr_done, batch_smem(threads));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_kernel, threads, batch_smem(threads));
+int batch_threads_max(int depth) {
+  return depth == 4 ? BatchDepth<4>::MAX_THREADS : (depth == 8 ? BatchDepth<8>::MAX_THREADS : 0);
 }
 
-cudaError_t launch_batch(const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
-                         int grain, int blocks, int threads, const BatchDebug& dbg, int* work,
+namespace {
+unsigned g_batch_attr_done[2];  // per depth (4, 8): devices with the shared-memory opt-in set
+size_t batch_smem(int depth, int threads) {
+  return stream_smem_bytes(false, depth, threads / 32, 1, BATCH_STAGES);
+}
+const void* batch_fn(int depth) {
+  return depth == 8 ? (const void*)batch_kernel<8> : (const void*)batch_kernel<4>;
+}
+}  // namespace
+
+cudaError_t batch_blocks_per_sm(int depth, int threads, int* out) {
+  if (batch_threads_max(depth) == 0) return cudaErrorInvalidValue;
+  cudaError_t e = ensure_smem_optin(batch_fn(depth), g_batch_attr_done[depth == 8], batch_smem(depth, threads));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_fn(depth), threads, batch_smem(depth, threads));
+}
+
+cudaError_t launch_batch(int depth, const cpb_grid_desc* descs, const int* order, int ngrids, int n_large,
+                         int bc, int grain, int blocks, int threads, const BatchDebug& dbg, int* work,
                          cudaStream_t s) {
-  const size_t shm = batch_smem(threads);
-  cudaError_t e = ensure_smem_optin((const void*)batch_kernel, g_batch_attr_done, shm);
+  if (batch_threads_max(depth) == 0 || threads > batch_threads_max(depth)) return cudaErrorInvalidValue;
+  const size_t shm = batch_smem(depth, threads);
+  cudaError_t e = ensure_smem_optin(batch_fn(depth), g_batch_attr_done[depth == 8], shm);
   if (e != cudaSuccess) return e;
   (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
   e = cudaMemsetAsync(work, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  batch_kernel<<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, dbg, work);
+  if (depth == 8)
+    batch_kernel<8><<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, dbg, work);
+  else
+    batch_kernel<4><<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, dbg, work);
   return cudaGetLastError();
 }
 

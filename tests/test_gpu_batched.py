@@ -66,7 +66,10 @@ def run_batch(L, grids, dev, bc, plan, u, k, s, off):
 @pytest.mark.parametrize("bc", [W.DIRICHLET, W.PERIODIC])
 @pytest.mark.parametrize("plan", [{"grain": 1, "blocks": 0, "threads": 384, "team_cells": 4096},
                                   {"grain": 3, "blocks": 3, "threads": 256, "team_cells": 20000},
-                                  {"grain": 2, "blocks": 0, "threads": 128, "team_cells": 1}])
+                                  {"grain": 2, "blocks": 0, "threads": 128, "team_cells": 1},
+                                  {"grain": 1, "blocks": 0, "threads": 256, "team_cells": 4096, "depth": 8},
+                                  {"grain": 2, "blocks": 5, "threads": 128, "team_cells": 20000,
+                                   "depth": 8}])
 def test_batched_bit_exact(dev, bc, plan):
     L = cpb.lib(fma=False)
     grids = small_batch(7 + bc, bc)
@@ -154,7 +157,8 @@ def test_batched_graph_capture(dev):
             np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref)
 
 
-def test_batched_ring_timeout_falls_back_and_is_reported(dev):
+@pytest.mark.parametrize("depth", [4, 8])   # single rows / rows in pairs
+def test_batched_ring_timeout_falls_back_and_is_reported(dev, depth):
     # One row's copies never complete (test hook) with a short wait limit:
     # the warps that meet it report CPB_ERR_TIMEOUT, redo the item with
     # ordinary loads, and every grid's result is still exact.
@@ -162,7 +166,7 @@ def test_batched_ring_timeout_falls_back_and_is_reported(dev):
     grids = [W.random_grid(40 + i, nx, ny, st, W.PERIODIC)
              for i, (nx, ny, st) in enumerate([(256, 40, 9), (128, 30, 6), (512, 20, 5), (96, 50, 7)])]
     u, k, s, off = pack(grids, dev)
-    plan = {"grain": 1, "blocks": 2, "threads": 128, "team_cells": 6000}
+    plan = {"grain": 1, "blocks": 2, "threads": 128, "team_cells": 6000, "depth": depth}
     uo = torch.full_like(u, -1.0)
     uin = u.clone()
     descs = cpb.batch_descriptors(uin, uo, k, s, off, [g.nx for g in grids],
@@ -209,8 +213,12 @@ def test_batch_autotune_picks_a_measured_plan_that_stays_exact(dev):
     best, table = L.cpb_batch_autotune(d_descs, d_order, len(grids), n_large, cpb.CPB_F32, bc, work,
                                        plan0)
     assert len(table) == cpb.BATCH_TUNE_CANDIDATES
-    assert all(v is not None and v > 0 for v in table.values())
-    assert (best["grain"], best["threads"]) in table
+    for (d, g, t), v in table.items():
+        if d == 8 and t > 256:
+            assert v is None                 # not a valid plan at depth 8
+        else:
+            assert v is not None and v > 0
+    assert table[(best["depth"], best["grain"], best["threads"])] is not None
     assert best["team_cells"] == plan0["team_cells"] and best["blocks"] == 0
     uo, _ = run_batch(L, grids, dev, bc, best, u, k, s, off)
     out = uo.cpu().numpy()

@@ -405,3 +405,16 @@ def test_bulk_variant_fma_build_within_tolerance(dev, fast):
                                    "stages": 8})
     err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("bc", [D, P])
+@pytest.mark.parametrize("k", [3, 8])
+def test_stream_kernel_equals_warp_level_oracle(dev, exact, bc, k):
+    # The tuned GPU kernel and the same kernel class run the paper's way for
+    # kernels with warp functions (nested warp / lane loops split at every
+    # shuffle), with the same depth and chunking: bit for bit.
+    g = W.random_grid(61 + k, 520, 77, 2 * k + 3, bc)
+    ref = oracle.strip_warp(g.u, g.kappa, g.src, g.steps, g.dt, bc, "f32", k=k, chunk=24, warps=2, pool=4)
+    got = run_tuned(exact, g, dev, {"k": k, "chunk_rows": 24, "warps_per_block": 2, "variant": 1,
+                                    "stages": 2})
+    np.testing.assert_array_equal(got, ref)
