@@ -197,39 +197,6 @@ __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); 
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
 
-// Packed FP32 pair arithmetic (sm_100+): each component is rounded exactly as
-// the scalar operation.  b - a is formed as fma(a, -1, b), which is exact in
-// the product and rounds once, i.e. the same bits as the subtraction.
-__device__ __forceinline__ float2 sub2(float2 b, float2 a) {
-  return __ffma2_rn(a, make_float2(-1.0f, -1.0f), b);
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-
-// In the build that reproduces the canonical order bit for bit, every packed
-// product is made opaque before it is used, so the compiler cannot fuse it
-// into a following addition (it does so for packed pairs even under
-// --fmad=false); the default build lets it fuse.
-__device__ __forceinline__ float2 round_product(float2 p) {
-#ifdef CPB_EXACT_ARITH
-  unsigned long long b = (unsigned long long)__float_as_uint(p.x) |
-                         ((unsigned long long)__float_as_uint(p.y) << 32);
-  asm volatile("" : "+l"(b));
-  return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
-#else
-  return p;
-#endif
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return round_product(__fmul2_rn(a, b)); }
-// h * acc + ds: fused in the default build; two roundings (product, then
-// sum) in the exact build.
-__device__ __forceinline__ float2 madd2(float2 h, float2 acc, float2 ds) {
-#ifdef CPB_EXACT_ARITH
-  return __fadd2_rn(mul2(h, acc), ds);
-#else
-  return __ffma2_rn(h, acc, ds);
-#endif
-}
-
 // BF16-Kahan rounding of two step results at once: hi = rn(v), cmp =
 // rn(hi - v), value hi - cmp; the same operations as kahan_round, with packed
 // conversions and differences.  words: (hi | cmp << 16) per cell.

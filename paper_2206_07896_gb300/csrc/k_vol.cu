@@ -353,16 +353,35 @@ __global__ void __launch_bounds__(256) vol_ring_kernel(const VolArgs a) {
       const float4 up = *reinterpret_cast<const float4*>(pp + r);
       const float4 kp = *reinterpret_cast<const float4*>(pp + KO + r);
       const float4 sc = *reinterpret_cast<const float4*>(pc + SO + ty * 128 + 4 * lane);
-      float4 o;
-      o.x = update7(uc.x, uWl, uc.y, uS.x, uN.x, um.x, up.x, kc.x, kWl, kc.y, kS.x, kN.x, km.x, kp.x, sc.x,
-                    dt, hdt);
-      o.y = update7(uc.y, uc.x, uc.z, uS.y, uN.y, um.y, up.y, kc.y, kc.x, kc.z, kS.y, kN.y, km.y, kp.y, sc.y,
-                    dt, hdt);
-      o.z = update7(uc.z, uc.y, uc.w, uS.z, uN.z, um.z, up.z, kc.z, kc.y, kc.w, kS.z, kN.z, km.z, kp.z, sc.z,
-                    dt, hdt);
-      o.w = update7(uc.w, uc.z, uEl, uS.w, uN.w, um.w, up.w, kc.w, kc.z, kEl, kS.w, kN.w, km.w, kp.w, sc.w,
-                    dt, hdt);
-      *reinterpret_cast<float4*>(a.uo + vidx(a, x0, y, z)) = o;
+      // The update of update7 on packed FP32 pairs (cells x, y and z, w): the
+      // y and z neighbours line up with the pairs; the x neighbours are the
+      // shifted pairs (W of x, x), (y, z) (east of the first pair, west of
+      // the second) and (w, E of w).
+      const float2 c0 = make_float2(uc.x, uc.y), c1 = make_float2(uc.z, uc.w);
+      const float2 k0 = make_float2(kc.x, kc.y), k1 = make_float2(kc.z, kc.w);
+      const float2 uw0 = make_float2(uWl, uc.x), kw0 = make_float2(kWl, kc.x);
+      const float2 umd = make_float2(uc.y, uc.z), kmd = make_float2(kc.y, kc.z);
+      const float2 ue1 = make_float2(uc.w, uEl), ke1 = make_float2(kc.w, kEl);
+      const float2 h2 = make_float2(hdt, hdt), dt2 = make_float2(dt, dt);
+      auto flux = [](float2 kcp, float2 knp, float2 ucp, float2 unp) {
+        return mul2(add2(kcp, knp), sub2(unp, ucp));
+      };
+      auto pair = [&](float2 c, float2 k, float2 uw, float2 kw, float2 ue, float2 ke, float2 us, float2 ks,
+                      float2 un, float2 kn, float2 ud, float2 kd, float2 uu, float2 ku, float2 s) {
+        const float2 acc = add2(add2(add2(flux(k, kw, c, uw), flux(k, ke, c, ue)),
+                                       add2(flux(k, ks, c, us), flux(k, kn, c, un))),
+                                 add2(flux(k, kd, c, ud), flux(k, ku, c, uu)));
+        return add2(c, madd2(h2, acc, mul2(dt2, s)));
+      };
+      const float2 o0 = pair(c0, k0, uw0, kw0, umd, kmd, make_float2(uS.x, uS.y), make_float2(kS.x, kS.y),
+                             make_float2(uN.x, uN.y), make_float2(kN.x, kN.y), make_float2(um.x, um.y),
+                             make_float2(km.x, km.y), make_float2(up.x, up.y), make_float2(kp.x, kp.y),
+                             make_float2(sc.x, sc.y));
+      const float2 o1 = pair(c1, k1, umd, kmd, ue1, ke1, make_float2(uS.z, uS.w), make_float2(kS.z, kS.w),
+                             make_float2(uN.z, uN.w), make_float2(kN.z, kN.w), make_float2(um.z, um.w),
+                             make_float2(km.z, km.w), make_float2(up.z, up.w), make_float2(kp.z, kp.w),
+                             make_float2(sc.z, sc.w));
+      *reinterpret_cast<float4*>(a.uo + vidx(a, x0, y, z)) = make_float4(o0.x, o0.y, o1.x, o1.y);
     }
   }
   cp_async_wait<0>();  // no copy may target this CTA's shared memory after it exits
