@@ -21,6 +21,9 @@ Functions (all numpy in, numpy out):
 * ``heat_sum_*``                      FP64 sums.
 * ``adjoint_f64``                     gradient of 0.5||u_T - target||^2 w.r.t.
                                       u_0 and kappa (discrete adjoint, checkpointed).
+* ``tile_blocked``                    the shared-memory temporal-blocked tiled
+                                      kernel (depth steps per launch, a
+                                      barrier after each) run with loop fission.
 * ``direct3`` / ``fission3``          the 3-D 7-point variant: the plain loop,
                                       and the z-marching tiled kernel (two
                                       barriers inside its plane loop) run with
@@ -79,6 +82,8 @@ def lib():
                                       C.POINTER(C.c_double)]
         L.orc_strip_warp_f32.argtypes = [_fp, _fp, _fp, i, i, i, f, i, i, i, i, i, i, _fp]
         L.orc_strip_warp_f64.argtypes = [_dp, _dp, _dp, i, i, i, d, i, i, i, i, i, i, _dp]
+        L.orc_tilek_f32.argtypes = [_fp, _fp, _fp, i, i, i, f, i, i, i, i, i, i, _fp]
+        L.orc_tilek_f64.argtypes = [_dp, _dp, _dp, i, i, i, d, i, i, i, i, i, i, _dp]
         L.orc_direct3_f32.argtypes = [_fp, _fp, _fp, i, i, i, i, f, i, i, _fp]
         L.orc_direct3_f64.argtypes = [_dp, _dp, _dp, i, i, i, i, d, i, i, _dp]
         L.orc_fission3_f32.argtypes = [_fp, _fp, _fp, i, i, i, i, f, i, i, i, i, i, _fp]
@@ -151,6 +156,20 @@ def strip_warp(u, kappa, src, steps, dt, bc, precision="f32", k=4, chunk=64, war
     dtv = float(dt) if precision == "f64" else float(np.float32(dt))
     _check(getattr(lib(), fn)(_c(u, T), _c(kappa, T), _c(src, T), nx, ny, steps, dtv, bc, k, chunk,
                               warps, pool, 1 if fission else 0, out), fn)
+    return out
+
+
+def tile_blocked(u, kappa, src, steps, dt, bc, precision="f32", depth=4, block=(32, 8), pool=1,
+                 fission=True):
+    """The shared-memory temporal-blocked tiled kernel (depth steps per
+    launch, depth + 1 barriers, depth of them inside its time loop) executed
+    with loop fission on the thread pool; fission=False ignores the barriers."""
+    ny, nx = u.shape
+    T, fn = (np.float64, "orc_tilek_f64") if precision == "f64" else (np.float32, "orc_tilek_f32")
+    out = np.empty((ny, nx), T)
+    dtv = float(dt) if precision == "f64" else float(np.float32(dt))
+    _check(getattr(lib(), fn)(_c(u, T), _c(kappa, T), _c(src, T), nx, ny, steps, dtv, bc, depth, block[0],
+                              block[1], pool, 1 if fission else 0, out), fn)
     return out
 
 

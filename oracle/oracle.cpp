@@ -37,6 +37,8 @@
 //    the 32 lanes of a warp, split at every shuffle (Sec. III-B).
 // 6. The 3-D 7-point variant: a direct loop and a z-marching tiled kernel
 //    with two barriers inside its plane loop, run with loop fission.
+// 7. A shared-memory temporal-blocked tiled kernel (K steps per launch,
+//    K + 1 barriers, K of them inside its time loop), run with loop fission.
 //
 // Build: g++ -O3 -ffp-contract=off (no FMA contraction: GCC contracts a*b+c
 // by default on aarch64, which would change the rounding order above).
@@ -401,6 +403,120 @@ int run_fission(const T* u0, const T* k, const T* s, int nx, int ny, int steps, 
     int rc = launch(stencil_tile_mpmd<T>, args, grid, Dim3{bx, by, 1}, shm, pool, block_per_fetch);
     if (rc) return rc;
     a.swap(b);
+  }
+  std::memcpy(out, a.data(), n * sizeof(T));
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// The shared-memory temporal-blocked tiled kernel: K steps per launch, K + 1
+// barriers, K of them inside the time loop (the multi-barrier class of the
+// paper's srad, Sec. V), translated with loop fission
+// ---------------------------------------------------------------------------
+// SPMD kernel (blockDim = (BX, BY); dynamic shared memory = four
+// (BX + 2K) x (BY + 2K) tiles of T: two u levels, kappa, s):
+//   R0:  the block's threads stage, in a strided loop over the tile, u, kappa
+//        and s of every tile position (tile origin (bx BX - K, by BY - K);
+//        boundary rule as in the one-step kernel, s = 0 on a Dirichlet ghost)
+//   __syncthreads();
+//   for t = 1 .. K:
+//     Rt: the threads update, in a strided loop, every position of the
+//         shrinking region [t, TW - t) x [t, TH - t) from level t - 1 into
+//         level t (the other u tile); a Dirichlet ghost position stays 0
+//     __syncthreads();
+//   RK+1: the threads write level K of the BX x BY interior (in-grid cells).
+// MPMD: the time loop is kept, and each barrier-free region -- R0, each Rt,
+// RK+1 -- becomes one loop over the block's threads.  fission = 0 runs all
+// regions of a thread before the next thread starts (barriers ignored), for
+// the test that shows the split is needed.
+template <class T>
+int stencil_tilek_mpmd(void** p) {
+  const T* u = *(const T**)p[0];
+  T* uo = *(T**)p[1];
+  const T* k = *(const T**)p[2];
+  const T* s = *(const T**)p[3];
+  const int nx = *(int*)p[4], ny = *(int*)p[5];
+  const T dt = *(T*)p[6], hdt = *(T*)p[7];
+  const int bc = *(int*)p[8], K = *(int*)p[9], fission = *(int*)p[10];
+  const int BX = block_size.x, BY = block_size.y, TW = BX + 2 * K, TH = BY + 2 * K;
+  const int nthreads = BX * BY, ntile = TW * TH;
+  const int bx = block_index % grid_size.x, by = block_index / grid_size.x;
+  const int gx0 = bx * BX - K, gy0 = by * BY - K;
+  const bool periodic = bc == BC_PERIODIC;
+  T* lev[2] = {(T*)dynamic_shared_memory, (T*)dynamic_shared_memory + ntile};
+  T* kt = lev[1] + ntile;
+  T* st = kt + ntile;
+  auto in_grid = [&](int gi, int gj) { return gi >= 0 && gi < nx && gj >= 0 && gj < ny; };
+  // region bodies for one thread
+  auto r0 = [&](int tid) {
+    for (int c = tid; c < ntile; c += nthreads) {
+      const int gi = gx0 + c % TW, gj = gy0 + c / TW;
+      stage(u, k, nx, ny, bc, gi, gj, lev[0], kt, c);
+      if (periodic)
+        st[c] = s[(size_t)wrap(gj, ny) * nx + wrap(gi, nx)];
+      else
+        st[c] = in_grid(gi, gj) ? s[(size_t)gj * nx + gi] : T(0);
+    }
+  };
+  auto rt = [&](int tid, int t) {
+    const T* a = lev[(t - 1) & 1];
+    T* b = lev[t & 1];
+    const int w = TW - 2 * t, h = TH - 2 * t;
+    for (int q = tid; q < w * h; q += nthreads) {
+      const int ti = t + q % w, tj = t + q / w, c = tj * TW + ti;
+      if (!periodic && !in_grid(gx0 + ti, gy0 + tj)) {
+        b[c] = T(0);
+        continue;
+      }
+      b[c] = cell_update<T>(a[c], a[c - 1], a[c + 1], a[c - TW], a[c + TW], kt[c], kt[c - 1], kt[c + 1],
+                            kt[c - TW], kt[c + TW], st[c], dt, hdt);
+    }
+  };
+  auto rlast = [&](int tid) {
+    const T* a = lev[K & 1];
+    for (int q = tid; q < nthreads; q += nthreads) {
+      const int ti = K + q % BX, tj = K + q / BX;
+      const int gi = gx0 + ti, gj = gy0 + tj;
+      if (gi < nx && gj < ny) uo[(size_t)gj * nx + gi] = a[tj * TW + ti];
+    }
+  };
+  if (fission) {
+    for (int tid = 0; tid < nthreads; ++tid) r0(tid);
+    // __syncthreads()
+    for (int t = 1; t <= K; ++t) {
+      for (int tid = 0; tid < nthreads; ++tid) rt(tid, t);
+      // __syncthreads()
+    }
+    for (int tid = 0; tid < nthreads; ++tid) rlast(tid);
+  } else {
+    for (int tid = 0; tid < nthreads; ++tid) {
+      r0(tid);
+      for (int t = 1; t <= K; ++t) rt(tid, t);
+      rlast(tid);
+    }
+  }
+  return 0;
+}
+
+// Passes of depth `depth` (the last takes the rest), one launch each.
+template <class T>
+int run_tilek(const T* u0, const T* k, const T* s, int nx, int ny, int steps, T dt, int bc, int depth,
+              int bx, int by, int pool, int fission, T* out) {
+  if (depth < 1 || bx < 1 || by < 1) return 1;
+  size_t n = (size_t)nx * ny;
+  T hdt = T(0.5) * dt;
+  std::vector<T> a(u0, u0 + n), b(n);
+  Dim3 grid{(nx + bx - 1) / bx, (ny + by - 1) / by, 1};
+  for (int done = 0; done < steps;) {
+    int d = std::min(depth, steps - done);
+    size_t shm = 4 * sizeof(T) * (size_t)(bx + 2 * d) * (by + 2 * d);
+    const T* ua = a.data();
+    T* ub = b.data();
+    void* args[11] = {&ua, &ub, &k, &s, &nx, &ny, &dt, &hdt, &bc, &d, &fission};
+    int rc = launch(stencil_tilek_mpmd<T>, args, grid, Dim3{bx, by, 1}, shm, pool, 0);
+    if (rc) return rc;
+    a.swap(b);
+    done += d;
   }
   std::memcpy(out, a.data(), n * sizeof(T));
   return 0;
@@ -1176,6 +1292,19 @@ int orc_strip_warp_f64(const double* u0, const double* k, const double* s, int n
                        double dt, int bc, int K, int chunk, int warps, int pool, int fission, double* out) {
   if (nx < 1 || ny < 1 || steps < 0) return 1;
   return run_strip_warp<double>(u0, k, s, nx, ny, steps, dt, bc, K, chunk, warps, pool, fission, out);
+}
+
+// The shared-memory temporal-blocked tiled kernel (multi-barrier).
+int orc_tilek_f32(const float* u0, const float* k, const float* s, int nx, int ny, int steps, float dt,
+                  int bc, int depth, int bx, int by, int pool, int fission, float* out) {
+  if (nx < 1 || ny < 1 || steps < 0) return 1;
+  return run_tilek<float>(u0, k, s, nx, ny, steps, dt, bc, depth, bx, by, pool, fission, out);
+}
+
+int orc_tilek_f64(const double* u0, const double* k, const double* s, int nx, int ny, int steps, double dt,
+                  int bc, int depth, int bx, int by, int pool, int fission, double* out) {
+  if (nx < 1 || ny < 1 || steps < 0) return 1;
+  return run_tilek<double>(u0, k, s, nx, ny, steps, dt, bc, depth, bx, by, pool, fission, out);
 }
 
 // 3-D 7-point variant.

@@ -3,8 +3,9 @@ hypothesis is not installed).
 
 Every executor of the paper's execution model -- the tiled kernel run with
 loop fission on the thread pool (Sec. III-B, Sec. IV), the warp-level strip
-kernel (nested warp / lane loops split at every shuffle, Sec. III-B) and the
-3-D z-marching kernel with barriers inside its plane loop -- must equal the
+kernel (nested warp / lane loops split at every shuffle, Sec. III-B), the
+3-D z-marching kernel with barriers inside its plane loop and the
+temporal-blocked tile with a barrier per time step -- must equal the
 direct loop (the stencil's definition) bit for bit for any grid shape, launch
 geometry, pool size, grain and depth.
 """
@@ -54,4 +55,15 @@ def test_fission3_equals_direct3(nx, ny, nz, steps, bc, bx, by, zc, pool, seed):
     ref = oracle.direct3(g.u, g.kappa, g.src, steps, g.dt, bc, "f32")
     got = oracle.fission3(g.u, g.kappa, g.src, steps, g.dt, bc, "f32", block=(bx, by), zchunks=min(zc, nz),
                           pool=pool)
+    np.testing.assert_array_equal(got, ref)
+
+
+@settings(max_examples=30, deadline=None)
+@given(nx=st.integers(1, 60), ny=st.integers(1, 30), steps=st.integers(0, 9), bc=bcs, depth=st.integers(1, 8),
+       bx=st.integers(1, 33), by=st.integers(1, 9), pool=st.integers(1, 4), seed=st.integers(0, 2 ** 16))
+def test_tile_blocked_equals_direct(nx, ny, steps, bc, depth, bx, by, pool, seed):
+    g = W.random_grid(seed, nx, ny, steps, bc)
+    ref = oracle.direct(g.u, g.kappa, g.src, steps, g.dt, bc, "f32")
+    got = oracle.tile_blocked(g.u, g.kappa, g.src, steps, g.dt, bc, "f32", depth=depth, block=(bx, by),
+                              pool=pool)
     np.testing.assert_array_equal(got, ref)
