@@ -6,7 +6,8 @@ at the autotuned temporal-block depth -- followed by the FP64 heat sum of the
 result.  Inputs (4 x 256 MiB) are larger than L2 and resident in HBM when the
 timed region starts.  The other forms of the path (BF16-Kahan storage at
 16384^2, the 4096-grid batch, the adjoint at 2048^2, the 3-D 7-point variant
-at 512^3) are reported under "forms" (skipped with --no-forms).
+at 512^3, the multi-barrier kernel at 8192^2) are reported under "forms"
+(skipped with --no-forms).
 
 Arms:
   default            the CUDA library (libcpb.so) through its C ABI.
@@ -435,10 +436,32 @@ def form_volume(L, cpb, dev, stream, n=512, steps=100):
             "note": "z-marching tiled kernel, one launch per step, default geometry (32 x 8 threads)"}
 
 
+def form_tile_blocked(L, cpb, dev, stream, n=8192):
+    """The multi-barrier kernel (shared-memory temporal blocking on the
+    caller's geometry) on the 8192^2 periodic workload, for a few geometries."""
+    import torch
+    g = W.plain_scale(seed=1, n=n, steps=1)
+    sh = stream.cuda_stream
+    u = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy(g.src).to(dev)
+    out, scr = torch.empty_like(u), torch.empty_like(u)
+    res = {}
+    for bx, by, d in ((32, 8, 1), (32, 16, 4), (64, 16, 8), (32, 32, 16)):
+        steps = 4 * d
+        geom = (((n + bx - 1) // bx, (n + by - 1) // by, 1), (bx, by, 1), L.cpb_tile_blocked_shared_bytes(bx, by, d))
+        ms = _time(lambda: L.cpb_stencil_tile_blocked(u, out, k, s, n, n, steps, d, float(g.dt), g.bc, *geom,
+                                                      scratch=scr, stream=sh), 2, stream)
+        res[f"block{bx}x{by}_depth{d}"] = {"gcells": n * n * steps / ms / 1e6, "us_per_step": ms / steps * 1e3}
+    return {"workload": f"plain-{n}x{n}-periodic", "geometries": res,
+            "note": "d steps per launch in shared memory, a __syncthreads after staging and after each step"}
+
+
 def measure_forms(L, cpb, dev, stream):
     out = {}
     for name, fn in (("precision", form_precision), ("batched", form_batched),
-                     ("adjoint", form_adjoint), ("volume", form_volume)):
+                     ("adjoint", form_adjoint), ("volume", form_volume),
+                     ("tile_blocked", form_tile_blocked)):
         try:
             out[name] = fn(L, cpb, dev, stream)
         except Exception as e:  # report, never lose the headline line

@@ -229,6 +229,28 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
                             cpb_dtype dtype, void* d_workspace, size_t ws_bytes,
                             cpb_stream_t stream);
 
+/* Shared-memory temporal blocking with the caller's geometry: the
+ * multi-barrier kernel class (the paper's srad has nine block
+ * synchronisations, Sec. V; its CPU translation needs loop fission with the
+ * time loop kept, Sec. III-B).  One launch advances `depth` steps (1..16): a
+ * block of block.x x block.y threads stages a (bx + 2 depth) x
+ * (by + 2 depth) tile of u, kappa and s, __syncthreads, then per step
+ * updates the shrinking region of the tile in shared memory and
+ * __syncthreads again, and finally writes its bx x by interior.  Same update,
+ * boundary rules, ping-pong and scratch semantics as cpb_stencil_launch
+ * (result always in u_out); CPB_F32 only; src may be NULL (s = 0).
+ * Geometry: block = (bx, by, 1) with bx * by <= 1024, else
+ * CPB_ERR_UNSUPPORTED_CONFIG; grid = (ceil(nx / bx), ceil(ny / by), 1), else
+ * CPB_ERR_INVALID_VALUE; shared_bytes >= cpb_tile_blocked_shared_bytes(bx,
+ * by, depth) (16 (bx + 2 depth)(by + 2 depth) bytes), else CPB_ERR_SHARED_MEM
+ * (more than 227 KB: CPB_ERR_UNSUPPORTED_CONFIG); depth outside 1..16:
+ * CPB_ERR_INVALID_VALUE.  Asynchronous on `stream`. */
+size_t cpb_tile_blocked_shared_bytes(int bx, int by, int depth); /* 0 if invalid */
+cpb_status cpb_stencil_tile_blocked(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                                    int ny, int steps, int depth, float dt, cpb_boundary bc, cpb_dim3 grid,
+                                    cpb_dim3 block, size_t shared_bytes, void* scratch,
+                                    cpb_stream_t stream);
+
 /* 3-D 7-point variant (the class of the paper's hotspot3D benchmark,
  * Sec. V): u'(x,y,z) from its six face neighbours, with the faces D (z-1)
  * and U (z+1) added to the 2-D update and rounded in the order

@@ -108,6 +108,9 @@ _SIGS = {
     "cpb_batch_work_bytes": (_sz, []),
     "cpb_stencil_batched": (_i, [_vp, _vp, _i, _i, _i, _i, C.POINTER(cpb_batch_plan), _vp, _vp]),
     "cpb_batch_status": (_i, [_vp, C.POINTER(_i), _vp]),
+    "cpb_tile_blocked_shared_bytes": (_sz, [_i, _i, _i]),
+    "cpb_stencil_tile_blocked": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _f, _i, cpb_dim3, cpb_dim3, _sz,
+                                      _vp, _vp]),
     "cpb_stencil3d_shared_bytes": (_sz, [_i]),
     "cpb_stencil3d_launch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _f, _i, cpb_dim3, cpb_dim3, _sz,
                                   _vp, _vp]),
@@ -201,6 +204,15 @@ class Library:
                            block, shared_bytes, scratch=None, stream=None):
         self._call("cpb_stencil_launch", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny, steps,
                    float(dt), bc, dtype, _dim3(grid), _dim3(block), shared_bytes, ptr(scratch),
+                   stream_handle(stream))
+
+    def cpb_tile_blocked_shared_bytes(self, bx, by, depth) -> int:
+        return self._lib.cpb_tile_blocked_shared_bytes(bx, by, depth)
+
+    def cpb_stencil_tile_blocked(self, u_in, u_out, kappa, src, nx, ny, steps, depth, dt, bc, grid, block,
+                                 shared_bytes, scratch=None, stream=None):
+        self._call("cpb_stencil_tile_blocked", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny, steps,
+                   depth, float(dt), bc, _dim3(grid), _dim3(block), shared_bytes, ptr(scratch),
                    stream_handle(stream))
 
     def cpb_stencil3d_shared_bytes(self, by) -> int:

@@ -337,6 +337,54 @@ cpb_status cpb_stencil_launch(void* u_in, void* u_out, const void* kappa, const 
   return enqueue_tile(f, nx, ny, steps, dt, bc, grid, block, shared_bytes, s);
 }
 
+size_t cpb_tile_blocked_shared_bytes(int bx, int by, int depth) {
+  if (bx < 1 || by < 1 || (long long)bx * by > 1024 || depth < 1 || depth > 16) return 0;
+  return tile_blocked_smem_bytes(bx, by, depth);
+}
+
+cpb_status cpb_stencil_tile_blocked(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                                    int ny, int steps, int depth, float dt, cpb_boundary bc, cpb_dim3 grid,
+                                    cpb_dim3 block, size_t shared_bytes, void* scratch,
+                                    cpb_stream_t stream) {
+  Fields f{u_in, u_out, kappa, src, scratch};
+  cpb_status st = check_common(f, nx, ny, steps, dt, bc, CPB_F32);
+  if (st != CPB_SUCCESS) return st;
+  if (depth < 1 || depth > 16) return CPB_ERR_INVALID_VALUE;
+  const long long bx = block.x, by = block.y;
+  if (block.z != 1 || bx < 1 || by < 1 || bx * by > 1024) return CPB_ERR_UNSUPPORTED_CONFIG;
+  if ((long long)grid.x != (nx + bx - 1) / bx || (long long)grid.y != (ny + by - 1) / by || grid.z != 1)
+    return CPB_ERR_INVALID_VALUE;
+  const size_t need = tile_blocked_smem_bytes((int)bx, (int)by, depth);
+  if (need > 227 * 1024) return CPB_ERR_UNSUPPORTED_CONFIG;
+  if (shared_bytes < need) return CPB_ERR_SHARED_MEM;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t ub = (size_t)nx * ny * sizeof(float);
+  if (steps == 0) {
+    CPB_TRY(cudaMemcpyAsync(u_out, u_in, ub, cudaMemcpyDeviceToDevice, s));
+    return CPB_SUCCESS;
+  }
+  bool copy_at_end = false;
+  std::vector<int> depths = pass_depths(steps, depth, scratch != nullptr, &copy_at_end);
+  const int P = (int)depths.size();
+  const void* src_buf = u_in;
+  for (int i = 0; i < P; ++i) {
+    void* dst;
+    if (scratch)
+      dst = ((P - 1 - i) % 2 == 0) ? u_out : scratch;
+    else if (!copy_at_end)
+      dst = ((P - 1 - i) % 2 == 0) ? u_out : u_in;
+    else
+      dst = (i % 2 == 0) ? u_out : u_in;
+    CPB_TRY(launch_tile_blocked_f32(static_cast<const float*>(src_buf), static_cast<float*>(dst),
+                                    static_cast<const float*>(kappa), static_cast<const float*>(src), nx, ny,
+                                    dt, (int)bc, depths[i], dim3(grid.x, grid.y, 1), dim3(block.x, block.y, 1),
+                                    s));
+    src_buf = dst;
+  }
+  if (copy_at_end) CPB_TRY(cudaMemcpyAsync(u_out, u_in, ub, cudaMemcpyDeviceToDevice, s));
+  return CPB_SUCCESS;
+}
+
 size_t cpb_stencil3d_shared_bytes(int by) { return (by >= 1 && by <= 8) ? vol_smem_bytes(by) : 0; }
 
 cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, const void* src, int nx,

@@ -55,6 +55,13 @@ cudaError_t launch_stream_bf16k(const StreamPass& p, int k, cudaStream_t s);
 cudaError_t read_stream_status_f32(int* out);
 cudaError_t read_stream_status_bf16k(int* out);
 
+// The shared-memory temporal-blocked tiled kernel (k_tile.cu): d steps per
+// launch, bx x by threads, four (bx + 2d) x (by + 2d) float tiles.
+size_t tile_blocked_smem_bytes(int bx, int by, int d);
+cudaError_t launch_tile_blocked_f32(const float* u_in, float* u_out, const float* kappa, const float* src,
+                                    int nx, int ny, float dt, int bc, int d, dim3 grid, dim3 block,
+                                    cudaStream_t s);
+
 // The tiled one-step kernel (bx x by threads, one cell each).
 cudaError_t launch_tile_f32(const float* u_in, float* u_out, const float* kappa, const float* src,
                             int nx, int ny, float dt, int bc, dim3 grid, dim3 block, size_t shm,
