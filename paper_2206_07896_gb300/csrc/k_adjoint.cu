@@ -113,22 +113,35 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS)
   const int xh = lane == 0 ? xs - 1 : xs + 128;
   const bool hin = periodic || (xh >= 0 && xh < nx);
   const int xhc = periodic ? wrap_index(xh, nx) : (xh < 0 ? 0 : (xh >= nx ? nx - 1 : xh));
-  Row3 S = load_row(y0 - 1), C = load_row(y0), N = load_row(y0 + 1);
-  for (int j = y0; j < y1; ++j) {
-    const Row3 NN = (j + 1 < y1) ? load_row(j + 2) : Row3{z4, z4, z4};
-    float hl = 0.f, hu = 0.f, hk = 0.f;
-    if ((lane == 0 || lane == 31) && hin) {
-      const size_t g = (size_t)j * nx + xhc;
+  // Row j's gradient accumulator and x-halo values, loaded one row ahead
+  // like the rows of lambda, u and kappa, so no load is waited for at its use.
+  auto load_gk = [&](int r) -> float4 {
+    return (r < y1 && x0 < nx) ? *reinterpret_cast<const float4*>(gk + (size_t)r * nx + x0) : z4;
+  };
+  auto load_halo = [&](int r, float& hl, float& hu, float& hk) {
+    hl = hu = hk = 0.f;
+    if ((lane == 0 || lane == 31) && hin && r < y1) {
+      const size_t g = (size_t)r * nx + xhc;
       hl = __ldg(lam + g);
       hu = __ldg(u + g);
       hk = __ldg(k + g);
     }
+  };
+  Row3 S = load_row(y0 - 1), C = load_row(y0), N = load_row(y0 + 1);
+  float4 g_cur = load_gk(y0);
+  float hl, hu, hk;
+  load_halo(y0, hl, hu, hk);
+  for (int j = y0; j < y1; ++j) {
+    const Row3 NN = (j + 1 < y1) ? load_row(j + 2) : Row3{z4, z4, z4};
+    const float4 g_next = load_gk(j + 1);
+    float hl_n, hu_n, hk_n;
+    load_halo(j + 1, hl_n, hu_n, hk_n);
     const float lW1 = __shfl_up_sync(0xffffffffu, C.l.w, 1), lE1 = __shfl_down_sync(0xffffffffu, C.l.x, 1);
     const float uW1 = __shfl_up_sync(0xffffffffu, C.u.w, 1), uE1 = __shfl_down_sync(0xffffffffu, C.u.x, 1);
     const float kW1 = __shfl_up_sync(0xffffffffu, C.k.w, 1), kE1 = __shfl_down_sync(0xffffffffu, C.k.x, 1);
     if (x0 < nx) {
       const size_t c0 = (size_t)j * nx + x0;
-      const float4 g_old = *reinterpret_cast<const float4*>(gk + c0);
+      const float4 g_old = g_cur;
       const bool iS = periodic || j - 1 >= 0, iN = periodic || j + 1 < ny;
       float lo[4], go[4];
 #pragma unroll
@@ -174,6 +187,10 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS)
     S = C;
     C = N;
     N = NN;
+    g_cur = g_next;
+    hl = hl_n;
+    hu = hu_n;
+    hk = hk_n;
   }
 }
 
