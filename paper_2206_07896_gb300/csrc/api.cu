@@ -42,7 +42,7 @@ cpb_status from_cuda(cudaError_t e) {
 
 bool aligned(const void* p, size_t a) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-size_t u_bytes(cpb_dtype d) { return 4; }                    // f32 or (hi, cmp) word
+size_t u_bytes(cpb_dtype) { return 4; }                    // f32 or (hi, cmp) word
 size_t ks_bytes(cpb_dtype d) { return d == CPB_F32 ? 4 : 2; }  // kappa / source element
 
 bool overlap(const void* a, const void* b, size_t n) {
