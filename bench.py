@@ -6,8 +6,9 @@ at the autotuned temporal-block depth -- followed by the FP64 heat sum of the
 result.  Inputs (4 x 256 MiB) are larger than L2 and resident in HBM when the
 timed region starts.  The other forms of the path (BF16-Kahan storage at
 16384^2, the 4096-grid batch, the adjoint at 2048^2, the 3-D 7-point variant
-at 512^3, the multi-barrier kernel at 8192^2) are reported under "forms"
-(skipped with --no-forms).
+at 512^3, the multi-barrier kernel at 8192^2, the 512^2 small workload with
+the tiled kernel, the tuned path and a CUDA-graph replay) are reported under
+"forms" (skipped with --no-forms).
 
 Arms:
   default            the CUDA library (libcpb.so) through its C ABI.
@@ -457,11 +458,45 @@ def form_tile_blocked(L, cpb, dev, stream, n=8192):
             "note": "d steps per launch in shared memory, a __syncthreads after staging and after each step"}
 
 
+def form_small(L, cpb, dev, stream):
+    """The small workload (512^2, Dirichlet, 100 steps, 16 x 16 blocks): the
+    paper-shaped one-step tiled kernel on the caller's geometry, the tuned
+    path, and the tuned path captured once as a CUDA graph and replayed
+    (L2-resident, so launch cost matters)."""
+    import torch
+    g = W.plain_small()
+    sh = stream.cuda_stream
+    n, T = g.nx, g.steps
+    u = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy(g.src).to(dev)
+    out, scr = torch.empty_like(u), torch.empty_like(u)
+    grid, block, shm = ((n + 15) // 16, (n + 15) // 16, 1), (16, 16, 1), 2 * 18 * 18 * 4
+    ms_tile = _time(lambda: L.cpb_stencil_launch(u, out, k, s, n, n, T, float(g.dt), g.bc, cpb.CPB_F32, grid,
+                                                 block, shm, scratch=scr, stream=sh), 5, stream)
+    tuning = L.cpb_get_tuning(n, n, cpb.CPB_F32, g.bc)
+    ms_tuned = _time(lambda: L.cpb_stencil_launch_tuned(u, out, k, s, n, n, T, float(g.dt), g.bc, cpb.CPB_F32,
+                                                        tuning=tuning, scratch=scr, stream=sh), 5, stream)
+    graph = L.cpb_graph_create(u, out, k, s, n, n, T, float(g.dt), g.bc, cpb.CPB_F32, tuning=tuning, scratch=scr)
+    try:
+        ms_graph = _time(lambda: L.cpb_graph_launch(graph, stream=sh), 5, stream)
+    finally:
+        L.cpb_graph_destroy(graph)
+    upd = n * n * T
+    passes = -(-T // tuning["k"])
+    return {"workload": g.name, "tiled_one_step_16x16": {"gcells": upd / ms_tile / 1e6, "ms": ms_tile,
+                                                         "launches": T},
+            "tuned": {"gcells": upd / ms_tuned / 1e6, "ms": ms_tuned, "launches": passes, "tuning": tuning},
+            "tuned_cuda_graph": {"gcells": upd / ms_graph / 1e6, "ms": ms_graph, "launches": passes},
+            "note": "4 MiB working set, L2-resident: HBM roofline not meaningful; the graph removes host "
+                    "launch cost"}
+
+
 def measure_forms(L, cpb, dev, stream):
     out = {}
     for name, fn in (("precision", form_precision), ("batched", form_batched),
                      ("adjoint", form_adjoint), ("volume", form_volume),
-                     ("tile_blocked", form_tile_blocked)):
+                     ("tile_blocked", form_tile_blocked), ("small", form_small)):
         try:
             out[name] = fn(L, cpb, dev, stream)
         except Exception as e:  # report, never lose the headline line
