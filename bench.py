@@ -69,7 +69,10 @@ def recorded_traffic(tuning, nx, ny):
     """DRAM bytes per launch of the stream kernel from the committed ncu record
     (profiles/stream_traffic.json: one entry per captured tuning), scaled to
     this grid by cell count; None if the kernel sources changed since the
-    counters were taken or no entry has this depth, variant and warps per CTA."""
+    counters were taken or no entry has this depth and row-load variant.  The
+    CTA shape and chunk height of the entry may differ from the autotuned
+    ones: the DRAM bytes per cell do not depend on them (16.13-16.16 over
+    every captured shape; halo re-reads come from L2)."""
     p = os.path.join(ROOT, "profiles", "stream_traffic.json")
     if not os.path.exists(p):
         return None
@@ -78,7 +81,7 @@ def recorded_traffic(tuning, nx, ny):
         return None
     for e in rec.get("entries", []):
         t = e.get("tuning", {})
-        if all(int(t.get(key, -1)) == int(tuning.get(key, -2)) for key in ("k", "variant", "warps_per_block")):
+        if all(int(t.get(key, -1)) == int(tuning.get(key, -2)) for key in ("k", "variant")):
             return float(e["dram_bytes_per_cell"]) * nx * ny
     return None
 
