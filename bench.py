@@ -461,6 +461,35 @@ def form_tile_blocked(L, cpb, dev, stream, n=8192):
             "note": "d steps per launch in shared memory, a __syncthreads after staging and after each step"}
 
 
+def form_depth1(L, cpb, dev, stream, n=8192):
+    """The plain streaming pass at depth 1 (no temporal blocking: 16 B of HBM
+    traffic per cell-update) on the 8192^2 periodic workload, over a few
+    tunings; the best one against the measured HBM copy rate.  This is the
+    bandwidth check of the streaming kernel itself: at depth 1 nothing hides
+    HBM."""
+    import torch
+    g = W.plain_scale(seed=1, n=n, steps=1)
+    sh = stream.cuda_stream
+    u = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy(g.src).to(dev)
+    out = torch.empty_like(u)
+    hbm, src = peaks()
+    res = {}
+    for c, w, v, st in ((128, 2, 1, 4), (256, 4, 1, 4), (256, 4, 1, 2), (128, 4, 1, 4), (256, 1, 0, 2)):
+        t = {"k": 1, "chunk_rows": c, "warps_per_block": w, "variant": v, "stages": st}
+        ms = _time(lambda: L.cpb_stencil_launch_tuned(u, out, k, s, n, n, 1, float(g.dt), g.bc, cpb.CPB_F32,
+                                                      tuning=t, stream=sh), 10, stream)
+        res[f"chunk{c}_wpb{w}_variant{v}_stages{st}"] = {"us_per_pass": ms * 1e3, "gcells": n * n / ms / 1e6,
+                                                         "tuning": t}
+    best = min(res.values(), key=lambda r: r["us_per_pass"])
+    gbs = 16.0 * n * n / (best["us_per_pass"] * 1e-6) / 1e9
+    return {"workload": f"plain-{n}x{n}-periodic", "tunings": res, "best": best,
+            "algorithmic_gbs": gbs, "frac_hbm": gbs / hbm, "peak": f"{hbm} GB/s ({src})",
+            "roofline_gcells": hbm * 1e9 / 16 / 1e9,
+            "note": "16 B per cell-update (u, kappa, s read, u written once per pass)"}
+
+
 def form_small(L, cpb, dev, stream):
     """The small workload (512^2, Dirichlet, 100 steps, 16 x 16 blocks): the
     paper-shaped one-step tiled kernel on the caller's geometry, the tuned
@@ -499,7 +528,7 @@ def measure_forms(L, cpb, dev, stream):
     out = {}
     for name, fn in (("precision", form_precision), ("batched", form_batched),
                      ("adjoint", form_adjoint), ("volume", form_volume),
-                     ("tile_blocked", form_tile_blocked), ("small", form_small)):
+                     ("tile_blocked", form_tile_blocked), ("small", form_small), ("depth_1", form_depth1)):
         try:
             out[name] = fn(L, cpb, dev, stream)
         except Exception as e:  # report, never lose the headline line
