@@ -31,6 +31,9 @@ Functions (all numpy in, numpy out):
 * ``strip_warp``                      the shuffle-based temporal-blocked strip
                                       kernel run with nested warp / lane loops
                                       split at every shuffle (Sec. III-B).
+* ``slab`` (module)                   the y-slab decomposition of the stencil
+                                      across ranks with K-row halo exchange every
+                                      K steps (torch.distributed gloo ranks on CPU).
 * ``vecadd`` / ``dynamic_reverse`` / ``fetch_accounting``
                                       the paper's example kernels (Listings 1-3)
                                       and runtime accounting, to test the executor.
