@@ -948,16 +948,55 @@ cpb_status cpb_adjoint_backward(const float* kappa, const float* src, const floa
   }
   cpb_tuning t1 = lookup_tuning(nx, ny, CPB_F32, bc);
   t1.k = 1;  // recompute one step per state
+  // Where the TMA row ring applies, a segment is recomputed by depth-4 passes
+  // that also store their intermediate levels: one pass reads the fields once
+  // and yields four consecutive states (12/4 + 4 B per cell and state instead
+  // of 16).  Slots are 256-byte aligned, so only the caller's fields decide.
+  const bool levels = bulk_eligible(nx, CPB_F32, nx % 4 == 0 && aligned(kappa, 16) && aligned(src, 16), kappa,
+                                    src);
+  StreamPass lp;
+  if (levels) {
+    const cpb_tuning t4 = default_tuning(nx, ny, CPB_F32);  // depth 4, TMA ring
+    lp.kappa = kappa;
+    lp.src = src;
+    lp.nx = nx;
+    lp.ny = ny;
+    lp.dt = dt;
+    lp.hdt = 0.5f * dt;
+    lp.bc = (int)bc;
+    lp.vec = 1;
+    lp.chunk_rows = t4.chunk_rows;
+    lp.warps_per_block = t4.warps_per_block;
+    lp.variant = 1;
+    lp.stages = t4.stages;
+    lp.wait_limit = g_wait_limit;
+    lp.inject_on = 0;
+    lp.inject_row = 0;
+    lp.store_levels = 1;
+  }
   const float* lam_cur = lambda_T;
   int flip = 0;
   for (int m = L.nseg - 1; m >= 0; --m) {
     const int len = std::min(ckpt_every, steps - m * ckpt_every);
     // states u_{a}, u_{a+1}, ..., u_{a+len-1}: the checkpoint, then recompute
-    for (int q = 1; q < len; ++q) {
-      void* prev = q == 1 ? (void*)L.ckpt(workspace, m) : (void*)L.seg(workspace, q - 2);
-      Fields f{prev, L.seg(workspace, q - 1), kappa, src, L.tmp(workspace)};
-      st = enqueue_tuned(f, nx, ny, 1, dt, bc, CPB_F32, t1, s);
-      if (st != CPB_SUCCESS) return st;
+    // (state q of the segment goes to slot seg(q - 1))
+    if (levels) {
+      for (int q = 1; q < len;) {
+        const int d = std::min(4, len - q);  // this pass yields states q .. q + d - 1
+        lp.u_in = q == 1 ? (const void*)L.ckpt(workspace, m) : (const void*)L.seg(workspace, q - 2);
+        for (int t = 1; t < d; ++t) lp.levels[t - 1] = L.seg(workspace, q + t - 2);
+        lp.u_out = L.seg(workspace, q + d - 2);
+        lp.depth = d;
+        CPB_TRY(launch_stream_f32(lp, 4, s));
+        q += d;
+      }
+    } else {
+      for (int q = 1; q < len; ++q) {
+        void* prev = q == 1 ? (void*)L.ckpt(workspace, m) : (void*)L.seg(workspace, q - 2);
+        Fields f{prev, L.seg(workspace, q - 1), kappa, src, L.tmp(workspace)};
+        st = enqueue_tuned(f, nx, ny, 1, dt, bc, CPB_F32, t1, s);
+        if (st != CPB_SUCCESS) return st;
+      }
     }
     for (int q = len - 1; q >= 0; --q) {
       const float* un = q == 0 ? L.ckpt(workspace, m) : L.seg(workspace, q - 1);

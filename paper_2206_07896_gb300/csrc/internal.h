@@ -25,6 +25,11 @@ struct StreamPass {
   int wait_limit;   // variant 1: mbarrier polls before a wait gives up
   int inject_on;    // variant 1, tests only: 1 = the copies of row inject_row never complete
   int inject_row;
+  // Depth 4, FP32, variant 1 only: also store level t (1..depth-1) of the
+  // pass to levels[t - 1] (each an nx*ny field), so one pass yields depth
+  // consecutive states.
+  int store_levels = 0;
+  float* levels[7] = {};
 };
 
 // Number of output columns per warp strip for temporal depth k (128 columns

@@ -62,6 +62,12 @@ struct StreamArgs {
   int inject_row;
 };
 
+// Level-storing kernel only: the rows of level t (1..depth-1) of a pass go to
+// p[t - 1] (each an nx x ny field).
+struct LevelOut {
+  float* p[7];
+};
+
 #define CPB_FULL 0xffffffffu
 
 // Device status word of this translation unit (CPB_ERR_TIMEOUT after a wait
@@ -632,9 +638,9 @@ __host__ __device__ constexpr bool rows_in_pairs(int k) { return k >= 6; }
 // the same body with run-time face slots.  Periodic refills walk a per-lane
 // source pointer row by row (one compare for the wrap) and expect a constant
 // byte count; Dirichlet refills go through issue_row (ghost rows).
-template <int K, bool BF, bool FULL, bool PERIODIC>
+template <int K, bool BF, bool FULL, bool PERIODIC, bool LV>
 __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int lane, unsigned char* ring,
-                                             uint64_t* bars, float4* face, int* status) {
+                                             uint64_t* bars, float4* face, int* status, const LevelOut* lv) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   constexpr bool periodic = PERIODIC;
@@ -738,6 +744,15 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
                                                             kn, sn, out, packed);
     if (i >= 2 * d && lane_store)  // output row r_in - d >= y0
       store_row<BF>(a.u_out, (size_t)(r_in - d) * nx, lc.xs, nx, true, out, packed);
+    if constexpr (LV) {  // also the rows of levels 1..d-1 that fall in this chunk
+#pragma unroll
+      for (int t = 1; t < K; ++t) {
+        const int rho = r_in - t;
+        if (t < d && rho >= y0 && rho < y1 && lane_store)
+          store_row<BF>(lv->p[t - 1], (size_t)rho * nx, lc.xs, nx, true,
+                        pipe.U[t][decltype(parity)::value], packed);
+      }
+    }
   };
   auto body = [&](auto parity, auto slot_c, int i) -> bool {
     float4 kn, un, sn;
@@ -803,11 +818,13 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
   return true;
 }
 
-template <int K, bool BF, bool FULL>
+template <int K, bool BF, bool FULL, bool LV = false>
 __device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lane, unsigned char* ring,
-                                          uint64_t* bars, float4* face, int* status) {
-  if (a.bc == BC_PERIODIC) return bulk_item_bc<K, BF, FULL, true>(a, item, lane, ring, bars, face, status);
-  return bulk_item_bc<K, BF, FULL, false>(a, item, lane, ring, bars, face, status);
+                                          uint64_t* bars, float4* face, int* status,
+                                          const LevelOut* lv = nullptr) {
+  if (a.bc == BC_PERIODIC)
+    return bulk_item_bc<K, BF, FULL, true, LV>(a, item, lane, ring, bars, face, status, lv);
+  return bulk_item_bc<K, BF, FULL, false, LV>(a, item, lane, ring, bars, face, status, lv);
 }
 
 // Shared memory of a CTA of `nwarps` warps using the row ring:
@@ -840,6 +857,22 @@ __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
     bulk_item<K, BF, false>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status);
 }
 
+// The same pass, also storing the rows of every intermediate level, so that a
+// pass of depth d yields d consecutive states (the adjoint's segment
+// recompute).  FP32 storage, TMA row ring.
+template <int K>
+__global__ void __launch_bounds__(256) stream_bulk_levels_kernel(const StreamArgs a, const LevelOut lv) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int item = blockIdx.x * nwarps + wib;
+  if (item >= a.n_items) return;  // warp-uniform; no block-level barrier is used
+  const BulkSmem<K, false> sm(smem, wib, nwarps, a.stages);
+  if (a.depth == K)
+    bulk_item<K, false, true, true>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status, &lv);
+  else
+    bulk_item<K, false, false, true>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status, &lv);
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -849,6 +882,7 @@ namespace {
 // unit and library (a function-local static of a template would be merged
 // across every shared object loaded in the process).
 unsigned g_smem_attr_done[2][2][9];
+unsigned g_smem_attr_levels_done;  // the level-storing kernel (depth 4, FP32)
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory, once per device.
 inline cudaError_t ensure_smem_optin(const void* fn, unsigned& done, size_t shm) {
@@ -903,6 +937,20 @@ cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
   const size_t face = (size_t)wpb * face_ring_rows(K) * FACE_SLOT_BYTES;
   const bool bulk = p.variant == 1;
   const size_t shm = face + (bulk ? bulk_smem_bytes(BF, wpb, p.stages) : 0);
+  if (p.store_levels) {  // built for depth 4, FP32, TMA row ring only
+    if constexpr (K == 4 && !BF) {
+      if (!bulk) return cudaErrorInvalidValue;
+      cudaError_t e = ensure_smem_optin((const void*)stream_bulk_levels_kernel<4>, g_smem_attr_levels_done, shm);
+      if (e != cudaSuccess) return e;
+      LevelOut lv;
+      for (int j = 0; j < 7; ++j) lv.p[j] = p.levels[j];
+      (void)cudaGetLastError();
+      stream_bulk_levels_kernel<4><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a, lv);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   cudaError_t e = ensure_smem_optin(bulk ? (const void*)stream_bulk_kernel<K, BF>
                                          : (const void*)stream_kernel<K, BF>,
                                     g_smem_attr_done[bulk ? 1 : 0][BF ? 1 : 0][K], shm);

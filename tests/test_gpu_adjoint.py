@@ -53,15 +53,22 @@ def test_adjoint_matches_fp64_oracle(dev, bc, shape, steps, ckpt):
         assert rel_l2(gk, gk_ref) <= 1e-4
 
 
-def test_adjoint_checkpoint_interval_invariant(dev):
-    g = W.differentiation(seed=3, n=200, ny=90, steps=31, ckpt=5)
+@pytest.mark.parametrize("bc", [W.DIRICHLET, W.PERIODIC])
+@pytest.mark.parametrize("nx,ny,steps,ckpts", [(200, 90, 31, (5, 31, 64)), (260, 70, 23, (2, 6, 23)),
+                                               (130, 40, 11, (3, 11))])
+def test_adjoint_checkpoint_interval_invariant(dev, bc, nx, ny, steps, ckpts):
+    # Checkpoints every step recompute nothing; longer intervals recompute
+    # each segment (depth-4 passes that store their levels where nx % 4 == 0,
+    # one-step passes otherwise) and must give the same bits.
+    g = W.differentiation(seed=3, n=nx, ny=ny, steps=steps, ckpt=5)
     lam_T = np.random.default_rng(0).standard_normal(g.u.shape)
-    L = cpb.lib(fma=False)
-    ref = gpu_adjoint(L, g, dev, 31, 1, W.DIRICHLET, lam_T)
-    for ck in (5, 31, 64):
-        got = gpu_adjoint(L, g, dev, 31, ck, W.DIRICHLET, lam_T)
+    L = cpb.lib(fma=False)  # the build whose rounding does not depend on the pass depth
+    ref = gpu_adjoint(L, g, dev, steps, 1, bc, lam_T)
+    for ck in ckpts:
+        got = gpu_adjoint(L, g, dev, steps, ck, bc, lam_T)
         np.testing.assert_array_equal(got[0], ref[0])
         np.testing.assert_array_equal(got[1], ref[1])
+    assert L.cpb_device_status() == 0
 
 
 def test_autograd_function(dev):
