@@ -367,7 +367,10 @@ cpb_status cpb_batch_autotune(const cpb_grid_desc* d_descs, const int* d_order, 
  *              boundary face.
  * The paper has no adjoint; this is the derivative of the update defined
  * above.  States are checkpointed every ckpt_every steps by the forward call
- * and each segment is recomputed during the backward sweep.
+ * and each segment is recomputed during the backward sweep: where the fields
+ * allow the TMA row path (nx % 4 == 0, nx >= 128, 16-byte aligned kappa and
+ * src), by depth-4 passes that store every intermediate state, otherwise one
+ * step per pass; either way the states equal those of a one-step run.
  *
  * workspace: device memory of cpb_adjoint_workspace_bytes() bytes, 256-byte
  * aligned, holding the checkpoints between cpb_adjoint_forward and
