@@ -12,6 +12,8 @@
 // kappa-gradient accumulation has no race): a per-cell form for any width,
 // and a row-marching form with 16-byte accesses for nx % 4 == 0.  The driver (api.cu) recomputes each checkpoint segment's states
 // with the forward kernels and then sweeps the segment backwards.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -66,12 +68,13 @@ __global__ void __launch_bounds__(ADJ_BX* ADJ_BY)
 
 // Row-marching form of the same step, for nx % 4 == 0 and 16-byte aligned
 // fields: a warp owns a strip of 128 columns (4 per lane, 16-byte accesses)
-// and a chunk of ADJ_ROWS rows, and keeps rows j-1, j, j+1 of lambda, u and
+// and a chunk of `rows` rows, and keeps rows j-1, j, j+1 of lambda, u and
 // kappa in registers while it marches down, so each value is read once per
 // step (the per-cell kernel reads every value five times).  x-neighbours come
 // by shuffle; the strip's edge columns from lanes 0 and 31.  Every cell is
-// computed with the per-cell kernel's expressions in the same order.
-constexpr int ADJ_ROWS = 8;
+// computed with the per-cell kernel's expressions in the same order.  The
+// chunk height is chosen at launch so the items fill about one wave of
+// resident warps (the result does not depend on it).
 constexpr int ADJ_WARPS = 4;
 
 struct Row3 {
@@ -89,13 +92,13 @@ __device__ __forceinline__ float comp(const float4& v, int e) {
 __global__ void __launch_bounds__(32 * ADJ_WARPS)
     adjoint_rows(const float* __restrict__ lam, float* __restrict__ lam_out, const float* __restrict__ u,
                  const float* __restrict__ k, float* __restrict__ gk, int nx, int ny, float dt, float hdt,
-                 int bc, int n_strips, int n_items) {
+                 int bc, int n_strips, int n_items, int rows) {
   const int lane = threadIdx.x & 31;
   const int item = blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
   if (item >= n_items) return;  // warp-uniform; no block-level barrier is used
   const int strip = item % n_strips, chunk = item / n_strips;
   const int xs = strip * 128, x0 = xs + 4 * lane;
-  const int y0 = chunk * ADJ_ROWS, y1 = min(ny, y0 + ADJ_ROWS);
+  const int y0 = chunk * rows, y1 = min(ny, y0 + rows);
   const bool periodic = bc == BC_PERIODIC;
   const int xv = periodic ? wrap_index(x0, nx) : (x0 < nx ? x0 : nx - 4);  // a valid 16-byte column
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -194,6 +197,29 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS)
   }
 }
 
+// Warps of adjoint_rows resident on the whole device, once per device
+// (ordinal < 32; others are queried on every call).
+int g_adj_resident[32];
+
+cudaError_t resident_warps(int* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && g_adj_resident[dev] > 0) {
+    *out = g_adj_resident[dev];
+    return cudaSuccess;
+  }
+  int sms = 0, per_sm = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_rows, 32 * ADJ_WARPS, 0);
+  if (e != cudaSuccess) return e;
+  const int w = std::max(1, sms * std::max(1, per_sm) * ADJ_WARPS);
+  if (dev < 32) g_adj_resident[dev] = w;
+  *out = w;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u, const float* k,
@@ -203,12 +229,19 @@ cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u
                        reinterpret_cast<uintptr_t>(gk);
   if (nx % 4 == 0 && al % 16 == 0) {
     const int n_strips = (nx + 127) / 128;
-    const long long items = (long long)n_strips * ((ny + ADJ_ROWS - 1) / ADJ_ROWS);
+    int warps = 0;
+    cudaError_t e = resident_warps(&warps);
+    if (e != cudaSuccess) return e;
+    // rows per item: the items come to about one wave of resident warps;
+    // at least 4 rows (the two halo rows are re-read per item)
+    const long long want = ((long long)n_strips * ny + warps - 1) / warps;
+    const int rows = (int)std::max(4LL, std::min(want, 1024LL));
+    const long long items = (long long)n_strips * ((ny + rows - 1) / rows);
     if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned blocks = (unsigned)((items + ADJ_WARPS - 1) / ADJ_WARPS);
     (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
     adjoint_rows<<<blocks, 32 * ADJ_WARPS, 0, s>>>(lam, lam_out, u, k, gk, nx, ny, dt, 0.5f * dt, bc, n_strips,
-                                                   (int)items);
+                                                   (int)items, rows);
     return cudaGetLastError();
   }
   dim3 block(ADJ_BX, ADJ_BY);
