@@ -33,7 +33,8 @@ Functions (all numpy in, numpy out):
                                       split at every shuffle (Sec. III-B).
 * ``slab`` (module)                   the y-slab decomposition of the stencil
                                       across ranks with K-row halo exchange every
-                                      K steps (torch.distributed gloo ranks on CPU).
+                                      K steps (torch.distributed gloo ranks, or
+                                      ranks as threads, on CPU).
 * ``vecadd`` / ``dynamic_reverse`` / ``fetch_accounting``
                                       the paper's example kernels (Listings 1-3)
                                       and runtime accounting, to test the executor.

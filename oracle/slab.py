@@ -105,6 +105,56 @@ class TorchDistExchange:
         return self._last
 
 
+class ThreadExchange:
+    """Ranks as threads of one process; each rank has a mailbox per direction.
+
+    ``make(world, periodic)`` returns one exchange object per rank; run each
+    rank's ``run_slab`` on its own thread."""
+
+    def __init__(self, rank, world, periodic, boxes):
+        self.rank, self.world = rank, world
+        self.lower = (rank - 1) % world if (periodic or rank > 0) else None
+        self.upper = (rank + 1) % world if (periodic or rank < world - 1) else None
+        self.boxes = boxes  # boxes[(dst, direction)]: "up" = sent by the rank below, "down" = by the rank above
+
+    @staticmethod
+    def make(world, periodic):
+        import queue
+        boxes = {(r, d): queue.Queue() for r in range(world) for d in ("up", "down")}
+        return [ThreadExchange(r, world, periodic, boxes) for r in range(world)]
+
+    def swap(self, to_lower, to_upper, timeout=60.0):
+        if self.upper is not None:
+            self.boxes[(self.upper, "up")].put(np.array(to_upper, copy=True))
+        if self.lower is not None:
+            self.boxes[(self.lower, "down")].put(np.array(to_lower, copy=True))
+        got_lower = self.boxes[(self.rank, "up")].get(timeout=timeout) if self.lower is not None else None
+        got_upper = self.boxes[(self.rank, "down")].get(timeout=timeout) if self.upper is not None else None
+        return got_lower, got_upper
+
+
+def run_threads(u, kappa, src, steps, dt, bc, K, world, precision="f32"):
+    """All ranks of the decomposition as threads; returns the assembled result."""
+    import threading
+    ex = ThreadExchange.make(world, bc == PERIODIC)
+    out, err = [None] * world, []
+
+    def rank_main(r):
+        try:
+            out[r] = run_slab(u, kappa, src, steps, dt, bc, K, r, world, ex[r], precision)
+        except Exception as e:  # reported to the caller below
+            err.append(e)
+
+    th = [threading.Thread(target=rank_main, args=(r,)) for r in range(world)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    if err:
+        raise err[0]
+    return np.concatenate(out, axis=0)
+
+
 def _step_rows(U, Kp, S, r0, r1, periodic_x, dt, hdt):
     """Return the updated rows [r0, r1) of the local arrays (one step, canonical order)."""
     c, kc = U[r0:r1], Kp[r0:r1]

@@ -1,7 +1,9 @@
 """Slab decomposition with halo exchange (the multi-GPU plan), on CPU ranks.
 
 Every run here has one GPU, so the library has no multi-GPU path; the
-decomposition itself is checked here, across torch.distributed gloo ranks.
+decomposition itself is checked here, across torch.distributed gloo ranks
+(processes) and across ranks run as threads of one process (randomised
+shapes, rank counts, depths and boundaries).
 Each rank owns a contiguous block of rows and exchanges K halo rows with its
 neighbours every K steps.  The assembled result must equal the direct update
 of the whole grid bit for bit, in FP32 and FP64, for periodic (a ring of
@@ -133,3 +135,28 @@ def test_too_few_rows_per_rank_is_rejected():
         slab.run_slab(g.u, g.kappa, g.src, 4, g.dt, g.bc, 3, 0, 2, slab.LocalExchange(True), "f32")
     with pytest.raises(ValueError):  # one periodic rank with fewer rows than K
         slab.run_slab(g.u, g.kappa, g.src, 4, g.dt, g.bc, 6, 0, 1, slab.LocalExchange(True), "f32")
+
+
+def test_thread_ranks_equal_direct():
+    # ranks as threads (mailbox per direction), a few fixed cases
+    for seed, nx, ny, steps, bc, K, world, prec in [(20, 30, 17, 9, W.PERIODIC, 3, 4, "f32"),
+                                                    (21, 9, 40, 13, W.DIRICHLET, 5, 7, "f64"),
+                                                    (22, 64, 8, 6, W.PERIODIC, 4, 2, "f32")]:
+        g = W.random_grid(seed, nx, ny, steps, bc)
+        res = slab.run_threads(g.u, g.kappa, g.src, steps, g.dt, bc, K, world, prec)
+        assert np.array_equal(res, oracle.direct(g.u, g.kappa, g.src, steps, g.dt, bc, prec))
+
+
+hypothesis = pytest.importorskip("hypothesis")
+st = hypothesis.strategies
+
+
+@hypothesis.settings(max_examples=40, deadline=None)
+@hypothesis.given(nx=st.integers(1, 24), world=st.integers(1, 5), K=st.integers(1, 6), extra=st.integers(0, 12),
+                  steps=st.integers(0, 15), bc=st.sampled_from([W.PERIODIC, W.DIRICHLET]),
+                  prec=st.sampled_from(["f32", "f64"]), seed=st.integers(0, 10 ** 6))
+def test_thread_ranks_random_shapes(nx, world, K, extra, steps, bc, prec, seed):
+    ny = world * K + extra  # every rank owns at least K rows
+    g = W.random_grid(seed, nx, ny, steps, bc)
+    res = slab.run_threads(g.u, g.kappa, g.src, steps, g.dt, bc, K, world, prec)
+    assert np.array_equal(res, oracle.direct(g.u, g.kappa, g.src, steps, g.dt, bc, prec))
