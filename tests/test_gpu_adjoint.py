@@ -53,19 +53,23 @@ def test_adjoint_matches_fp64_oracle(dev, bc, shape, steps, ckpt):
         assert rel_l2(gk, gk_ref) <= 1e-4
 
 
+@pytest.mark.parametrize("with_src", [False, True])
 @pytest.mark.parametrize("bc", [W.DIRICHLET, W.PERIODIC])
 @pytest.mark.parametrize("nx,ny,steps,ckpts", [(200, 90, 31, (5, 31, 64)), (260, 70, 23, (2, 6, 23)),
                                                (130, 40, 11, (3, 11))])
-def test_adjoint_checkpoint_interval_invariant(dev, bc, nx, ny, steps, ckpts):
+def test_adjoint_checkpoint_interval_invariant(dev, bc, nx, ny, steps, ckpts, with_src):
     # Checkpoints every step recompute nothing; longer intervals recompute
     # each segment (depth-4 passes that store their levels where nx % 4 == 0,
-    # one-step passes otherwise) and must give the same bits.
+    # one-step passes otherwise) and must give the same bits, with or
+    # without a source term in the states.
     g = W.differentiation(seed=3, n=nx, ny=ny, steps=steps, ckpt=5)
-    lam_T = np.random.default_rng(0).standard_normal(g.u.shape)
+    rng = np.random.default_rng(0)
+    lam_T = rng.standard_normal(g.u.shape)
+    src = (rng.random(g.u.shape, dtype=np.float32) * np.float32(1e-3)) if with_src else None
     L = cpb.lib(fma=False)  # the build whose rounding does not depend on the pass depth
-    ref = gpu_adjoint(L, g, dev, steps, 1, bc, lam_T)
+    ref = gpu_adjoint(L, g, dev, steps, 1, bc, lam_T, src=src)
     for ck in ckpts:
-        got = gpu_adjoint(L, g, dev, steps, ck, bc, lam_T)
+        got = gpu_adjoint(L, g, dev, steps, ck, bc, lam_T, src=src)
         np.testing.assert_array_equal(got[0], ref[0])
         np.testing.assert_array_equal(got[1], ref[1])
     assert L.cpb_device_status() == 0
