@@ -211,18 +211,33 @@ cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* 
 cpb_status cpb_heat_sum_noalloc(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
                                 cpb_stream_t stream);
 
-/* BF16 conversions on the device (round to nearest even).
+/* BF16 conversions on the device (IEEE round to nearest even), for moving
+ * fields in and out of the CPB_BF16_KAHAN storage format.  The paper has no
+ * reduced-precision storage; the format is this library's (one 32-bit word
+ * per cell: the bf16 value hi in the low half, the bf16 compensation cmp in
+ * the high half, represented value hi - cmp).
  * cpb_bf16_round: out[i] = rn_bf16(x[i]) (bf16 bit patterns).
  * cpb_bf16k_pack: state[i] = hi | cmp << 16 with hi = rn(u), cmp = rn(hi - u).
- * cpb_bf16k_unpack: u[i] = (float)hi - (float)cmp. */
+ * cpb_bf16k_unpack: u[i] = (float)hi - (float)cmp.
+ * n elements; all pointers caller-owned device memory, 4-byte (2-byte for
+ * out) aligned.  n < 0, or n > 0 with a null pointer: CPB_ERR_INVALID_VALUE;
+ * n == 0 does nothing.  Asynchronous on `stream`. */
 cpb_status cpb_bf16_round(const float* x, uint16_t* out, long long n, cpb_stream_t stream);
 cpb_status cpb_bf16k_pack(const float* u, uint32_t* state, long long n, cpb_stream_t stream);
 cpb_status cpb_bf16k_unpack(const uint32_t* state, float* u, long long n, cpb_stream_t stream);
 
-/* End-to-end call on HOST buffers: copies u0, kappa, src in (pinned host
+/* End-to-end call on HOST buffers (the paper's timings include the
+ * host <-> device transfers, Sec. V "Performance"): copies u0, kappa, src in (pinned host
  * memory gives asynchronous copies), runs `steps` steps on the tuned path,
- * copies the result to u_out_host and synchronises `stream`.  d_workspace:
- * device memory of at least cpb_host_workspace_bytes(nx, ny, dtype). */
+ * copies the result to u_out_host and synchronises `stream` before it
+ * returns.  Host buffers: caller-owned, nx * ny elements of the storage
+ * format (u as for cpb_stencil_launch, kappa and src float for CPB_F32 and
+ * bf16 for CPB_BF16_KAHAN), read or written only during the call; src may be
+ * NULL (s = 0).  d_workspace: caller-owned device memory, 256-byte aligned,
+ * of at least cpb_host_workspace_bytes(nx, ny, dtype) bytes (0 for invalid
+ * sizes), else CPB_ERR_WORKSPACE.  Null host pointers, sizes below 1, an
+ * unknown dtype and the argument errors of cpb_stencil_launch_tuned:
+ * CPB_ERR_INVALID_VALUE. */
 size_t cpb_host_workspace_bytes(int nx, int ny, cpb_dtype dtype);
 cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const void* src_host,
                             void* u_out_host, int nx, int ny, int steps, float dt, cpb_boundary bc,
