@@ -24,7 +24,7 @@
  * Sec. IV "Push task queue"): the caller supplies launch geometry (grid,
  * block, dynamic shared bytes) as in <<<grid, block, shm>>> and the fields of
  * the paper's kernel structure (Listing 6); every call only enqueues work on
- * the caller's stream and returns (asynchronous launch, Sec. III-C "Implicit
+ * the caller's stream and returns (asynchronous launch, Sec. III "Implicit
  * barrier insertion": the caller synchronises before reading results on the
  * host).  Errors are status codes, never exceptions.
  *
@@ -247,7 +247,7 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
 /* Shared-memory temporal blocking with the caller's geometry: the
  * multi-barrier kernel class (the paper's srad has nine block
  * synchronisations, Sec. V; its CPU translation needs loop fission with the
- * time loop kept, Sec. III-B).  One launch advances `depth` steps (1..16): a
+ * time loop kept, Sec. III "SPMD to MPMD").  One launch advances `depth` steps (1..16): a
  * block of block.x x block.y threads stages a (bx + 2 depth) x
  * (by + 2 depth) tile of u, kappa and s, __syncthreads, then per step
  * updates the shrinking region of the tile in shared memory and

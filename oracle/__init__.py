@@ -14,7 +14,7 @@ Functions (all numpy in, numpy out):
                                       blocks run by a thread pool with a task queue
                                       and coarse-grained fetching (Sec. IV), and
                                       inside each block one thread loop per
-                                      barrier-free region (Sec. III-B).
+                                      barrier-free region (Sec. III "SPMD to MPMD").
 * ``direct_bf16k``                    BF16-Kahan storage, FP32 compute.
 * ``sample``                          sampled cells of a large run via their
                                       dependency cones (bit-identical to ``direct``).
@@ -30,7 +30,7 @@ Functions (all numpy in, numpy out):
                                       loop fission.
 * ``strip_warp``                      the shuffle-based temporal-blocked strip
                                       kernel run with nested warp / lane loops
-                                      split at every shuffle (Sec. III-B).
+                                      split at every shuffle (Sec. III "SPMD to MPMD").
 * ``slab`` (module)                   the y-slab decomposition of the stencil
                                       across ranks with K-row halo exchange every
                                       K steps (torch.distributed gloo ranks, or
@@ -152,7 +152,7 @@ def strip_warp(u, kappa, src, steps, dt, bc, precision="f32", k=4, chunk=64, war
     """The shuffle-based temporal-blocked strip kernel (a warp per 128-column
     strip, 4 cells per lane, k time levels per pass) executed per the paper's
     execution model for kernels with warp-level functions: nested warp / lane
-    loops split at every shuffle (Sec. III-B).  fission=False ignores the
+    loops split at every shuffle (Sec. III "SPMD to MPMD").  fission=False ignores the
     split at the shuffles (for the test showing it is needed).  k <= 8."""
     ny, nx = u.shape
     T, fn = (np.float64, "orc_strip_warp_f64") if precision == "f64" else (np.float32, "orc_strip_warp_f32")

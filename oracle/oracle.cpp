@@ -19,9 +19,9 @@
 //    CPU: the tiled SPMD kernel (one thread per cell, a shared (BX+2)x(BY+2)
 //    halo tile of u and kappa, one __syncthreads) is turned into an explicit
 //    loop over the threads of a block, split into one loop per barrier-free
-//    region ("SPMD to MPMD", Sec. III-B), with launch geometry held in
-//    explicitly inserted variables (Sec. III-B, "Extra variable insertion"),
-//    parameters packed into a void** (Sec. III-C, "Parameter packing",
+//    region ("SPMD to MPMD", Sec. III), with launch geometry held in
+//    explicitly inserted variables (Sec. III, "Extra variable insertion"),
+//    parameters packed into a void** (Sec. III, "Parameter packing",
 //    Listing 5), and blocks run by a pthread pool fed by a mutex-protected
 //    task queue of kernel structures (Sec. IV, Listing 6) with average
 //    coarse-grained fetching, ceil(gridSize / poolSize) blocks per fetch
@@ -34,7 +34,7 @@
 // 5. A shuffle-based, temporal-blocked strip kernel (a warp per 128-column
 //    strip, K time levels per pass) executed the way the paper runs kernels
 //    with warp-level functions: nested loops over the warps of a block and
-//    the 32 lanes of a warp, split at every shuffle (Sec. III-B).
+//    the 32 lanes of a warp, split at every shuffle (Sec. III "SPMD to MPMD").
 // 6. The 3-D 7-point variant: a direct loop and a z-marching tiled kernel
 //    with two barriers inside its plane loop, run with loop fission.
 // 7. A shared-memory temporal-blocked tiled kernel (K steps per launch,
@@ -85,7 +85,7 @@ struct KernelTask {
 };
 
 // Per-worker launch context, assigned by the runtime before each block runs
-// (Sec. III-B "Extra variable insertion", Listing 7).  The paper's listing
+// (Sec. III "Extra variable insertion", Listing 7).  The paper's listing
 // assigns the block *size* from totalBlocks; the reading taken here is the
 // block dimension.
 thread_local int block_index;
@@ -347,7 +347,7 @@ inline void stage(const T* u, const T* k, int nx, int ny, int bc, int gi, int gj
 
 template <class T>
 int stencil_tile_mpmd(void** p) {
-  // Unpacking prologue (Sec. III-C, parameter packing).
+  // Unpacking prologue (Sec. III, "Parameter packing").
   const T* u = *(const T**)p[0];
   T* uo = *(T**)p[1];
   const T* k = *(const T**)p[2];
@@ -646,7 +646,7 @@ int count_mpmd(void** p) {
 
 // ---------------------------------------------------------------------------
 // Warp-level kernel: a shuffle-based, temporal-blocked strip kernel executed
-// with nested loops split at every warp function (Sec. III-B: a kernel that
+// with nested loops split at every warp function (Sec. III "SPMD to MPMD": a kernel that
 // uses warp-level features is wrapped in an outer loop over the
 // ceil(block_size / 32) warps of a block and an inner loop over the 32 lanes
 // of a warp, one such nest per code section between warp functions)

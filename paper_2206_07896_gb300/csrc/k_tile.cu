@@ -1,7 +1,7 @@
 // The tiled one-step stencil kernel: one thread per cell, a (bx+2) x (by+2)
 // shared tile of u and of kappa with a one-cell halo, one __syncthreads.
 //
-// This is the kernel class the paper translates for CPUs (Sec. III-B): its
+// This is the kernel class the paper translates for CPUs (Sec. III "SPMD to MPMD"): its
 // two barrier-free regions -- stage the tile, then update from the tile --
 // are what the CPU executor turns into two thread loops ("loop fission").
 // Launch geometry is the caller's (<<<grid, block, shm>>>), one launch per step.

@@ -1,6 +1,6 @@
 """Pins for the oracle's execution model (the paper's CPU runtime).
 
-The executor follows the paper's SPMD-to-MPMD scheme (Sec. III-B: one loop over
+The executor follows the paper's SPMD-to-MPMD scheme (Sec. III "SPMD to MPMD": one loop over
 a block's threads per barrier-free region) and its runtime (Sec. IV: thread pool,
 mutex task queue of kernel structures, coarse-grained fetching).  Each test pins
 it to a result fixed by definition, not by the oracle itself.

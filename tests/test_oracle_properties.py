@@ -2,8 +2,8 @@
 hypothesis is not installed).
 
 Every executor of the paper's execution model -- the tiled kernel run with
-loop fission on the thread pool (Sec. III-B, Sec. IV), the warp-level strip
-kernel (nested warp / lane loops split at every shuffle, Sec. III-B), the
+loop fission on the thread pool (Sec. III "SPMD to MPMD", Sec. IV), the warp-level strip
+kernel (nested warp / lane loops split at every shuffle, Sec. III "SPMD to MPMD"), the
 3-D z-marching kernel with barriers inside its plane loop and the
 temporal-blocked tile with a barrier per time step -- must equal the
 direct loop (the stencil's definition) bit for bit for any grid shape, launch

@@ -1,7 +1,7 @@
 """Pins for the multi-barrier kernel in the oracle: the shared-memory
 temporal-blocked tiled kernel (depth steps per launch, depth + 1 barriers,
 depth of them inside its time loop -- the paper's srad class has nine block
-synchronisations, Sec. V) executed with loop fission (Sec. III-B): the time
+synchronisations, Sec. V) executed with loop fission (Sec. III "SPMD to MPMD"): the time
 loop is kept and each barrier-free region inside it becomes a thread loop.
 
 Pinned to the direct loop bit for bit over depths, block shapes, ragged

@@ -1,6 +1,6 @@
 """Pins for the warp-level executor of the oracle.
 
-Sec. III-B: a kernel that uses warp-level functions (shuffles) is wrapped in
+Sec. III "SPMD to MPMD": a kernel that uses warp-level functions (shuffles) is wrapped in
 nested loops -- an outer loop over the ceil(block_size / 32) warps of a block
 and an inner loop over the 32 lanes of a warp -- split at every warp function.
 The oracle runs the shuffle-based, temporal-blocked strip kernel (a warp per
