@@ -719,6 +719,153 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Profiling mode: one launch per configuration, for ncu captures
+# ---------------------------------------------------------------------------
+def _profile_fields(dev, g):
+    import torch
+    return (torch.from_numpy(g.u).to(dev), torch.from_numpy(g.kappa).to(dev),
+            torch.from_numpy(g.src).to(dev))
+
+
+def profile_stream(L, cpb, dev, args):
+    """ONE pass of depth K per --spec K:chunk:wpb:variant:stages on the n x n
+    workload (periodic plain_scale fields, or the precision workload's fields
+    with --bc dirichlet), FP32 or BF16-Kahan storage (--dtype)."""
+    import torch
+    n = args.n
+    if args.bc == "dirichlet":
+        g = W.precision(n=n, steps=16)
+    else:
+        g = W.plain_scale(seed=1, n=n, steps=16)
+    u, k, s = _profile_fields(dev, g)
+    dtype = cpb.CPB_F32
+    if args.dtype == "bf16k":
+        N = n * n
+        st = torch.empty(N, dtype=torch.int32, device=dev)
+        kb = torch.empty(N, dtype=torch.int16, device=dev)
+        sb = torch.empty(N, dtype=torch.int16, device=dev)
+        L.cpb_bf16k_pack(u, st, N)
+        L.cpb_bf16_round(k, kb, N)
+        L.cpb_bf16_round(s, sb, N)
+        u, k, s, dtype = st, kb, sb, cpb.CPB_BF16_KAHAN
+    out = torch.empty_like(u)
+    for sp in args.spec or ["4:256:1:1:2"]:
+        K, c, w, v, stg = (int(x) for x in sp.split(":"))
+        t = {"k": K, "chunk_rows": c, "warps_per_block": w, "variant": v, "stages": stg}
+        L.cpb_stencil_launch_tuned(u, out, k, s, n, n, K, float(g.dt), g.bc, dtype, tuning=t)
+    torch.cuda.synchronize()
+    return L.cpb_device_status()
+
+
+def profile_vol(L, cpb, dev, args):
+    """ONE step of cpb_stencil3d_launch per --spec by:zchunks on the n^3 volume."""
+    import torch
+    n = args.n
+    if n > 1024:
+        raise SystemExit("--profile vol: --n is the cube side, at most 1024")
+    g = W.volume(n=n, steps=1)
+    u, k, s = _profile_fields(dev, g)
+    out = torch.empty_like(u)
+    for sp in args.spec or ["8:16"]:
+        by, zc = (int(x) for x in sp.split(":"))
+        L.cpb_stencil3d_launch(u, out, k, s, n, n, n, 1, float(g.dt), g.bc,
+                               ((n + 127) // 128, (n + by - 1) // by, zc), (32, by, 1),
+                               L.cpb_stencil3d_shared_bytes(by))
+    torch.cuda.synchronize()
+    return L.cpb_device_status()
+
+
+def profile_tileb(L, cpb, dev, args):
+    """ONE launch of the multi-barrier kernel per --spec bx:by:depth."""
+    import torch
+    n = args.n
+    g = W.plain_scale(seed=1, n=n, steps=1)
+    u, k, s = _profile_fields(dev, g)
+    out, scr = torch.empty_like(u), torch.empty_like(u)
+    for sp in args.spec or ["64:16:8"]:
+        bx, by, d = (int(x) for x in sp.split(":"))
+        L.cpb_stencil_tile_blocked(u, out, k, s, n, n, d, d, float(g.dt), g.bc,
+                                   ((n + bx - 1) // bx, (n + by - 1) // by, 1), (bx, by, 1),
+                                   L.cpb_tile_blocked_shared_bytes(bx, by, d), scratch=scr)
+    torch.cuda.synchronize()
+    return L.cpb_device_status()
+
+
+def profile_adjoint(L, cpb, dev, args):
+    """ONE gradient of the 2048^2 differentiation workload, as the bench times it."""
+    import torch
+    g = W.differentiation()
+    nx, ny, T, ck = g.nx, g.ny, g.steps, g.extras["ckpt"]
+    u0 = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    tgt = torch.from_numpy(g.extras["target"]).to(dev)
+    wsb = L.cpb_adjoint_workspace_bytes(nx, ny, T, ck)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    uT, gu, gk = torch.empty_like(u0), torch.empty_like(u0), torch.empty_like(u0)
+    L.cpb_adjoint_forward(u0, k, None, nx, ny, T, float(g.dt), g.bc, ck, uT, ws, wsb)
+    lam = uT - tgt
+    L.cpb_adjoint_backward(k, None, lam, nx, ny, T, float(g.dt), g.bc, ck, gu, gk, ws, wsb)
+    torch.cuda.synchronize()
+    return L.cpb_device_status()
+
+
+def profile_batch(L, cpb, dev, args):
+    """ONE batched persistent launch over the --n cheapest grids (by
+    cell-updates) of the 4096-grid set, default plan: a subset of cheap grids
+    keeps every grid far below the per-SM share, so no single grid sets the
+    length of the launch."""
+    import ctypes as C
+    import torch
+    n = args.n
+    if not 1 <= n <= 4096:
+        raise SystemExit("--profile batch: --n is the number of grids, 1..4096")
+    bt = W.batching(ngrids=4096)
+    sel = np.sort(np.argsort(bt.nx.astype(np.int64) * bt.ny * bt.steps, kind="stable")[:n])
+    nx, ny, steps, dt = bt.nx[sel], bt.ny[sel], bt.steps[sel], bt.dt[sel]
+    cells = nx.astype(np.int64) * ny.astype(np.int64)
+    off = np.zeros(n, np.int64)
+    off[1:] = np.cumsum((cells + 3) // 4 * 4)[:-1]  # 16-byte aligned grid starts
+    total = int(off[-1] + cells[-1])
+    u = torch.zeros(total, dtype=torch.float32, device=dev)
+    k = torch.ones(total, dtype=torch.float32, device=dev)
+    s = torch.zeros(total, dtype=torch.float32, device=dev)
+    for q, gi in enumerate(sel):
+        o, c, b = int(off[q]), int(cells[q]), int(bt.offset[gi])
+        u[o:o + c] = torch.from_numpy(bt.u[b:b + c])
+        k[o:o + c] = torch.from_numpy(bt.kappa[b:b + c])
+        s[o:o + c] = torch.from_numpy(bt.src[b:b + c])
+    uo = torch.empty_like(u)
+    descs = cpb.batch_descriptors(u, uo, k, s, off, nx, ny, steps, dt)
+    plan = L.cpb_batch_plan_default()
+    order, n_large = L.cpb_batch_order(descs, plan)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+    L.cpb_stencil_batched(d_descs, d_order, n, n_large, cpb.CPB_F32, W.DIRICHLET, plan, work)
+    torch.cuda.synchronize()
+    return L.cpb_batch_status(work)
+
+
+PROFILES = {"stream": profile_stream, "vol": profile_vol, "tileb": profile_tileb,
+            "adjoint": profile_adjoint, "batch": profile_batch}
+
+
+def run_profile(args):
+    """--profile KIND: a handful of launches of one kernel family and nothing
+    else, so that `ncu -k regex:<kernel> -c <count>` captures exactly those
+    launches.  Prints one line; exits 1 on a non-zero device status."""
+    import torch
+    import paper_2206_07896_gb300 as cpb
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    L = cpb.lib(fma=True)
+    status = PROFILES[args.profile](L, cpb, dev, args)
+    print(f"profile {args.profile} n={args.n} specs={args.spec} dtype={args.dtype} bc={args.bc} "
+          f"status {status}", flush=True)
+    return 0 if status == 0 else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -738,7 +885,17 @@ def main(argv=None):
                     help="skip the BF16 / batched / adjoint forms")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, choices=sorted(PROFILES),
+                    help="profiling mode: one launch per --spec of one kernel family (for ncu)")
+    ap.add_argument("--spec", action="append", default=None,
+                    help="--profile geometry: stream K:chunk:wpb:variant:stages, vol by:zchunks, "
+                         "tileb bx:by:depth (repeatable)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16k"], help="--profile stream storage")
+    ap.add_argument("--bc", default="periodic", choices=["periodic", "dirichlet"],
+                    help="--profile stream boundary (dirichlet: the precision workload's fields)")
     args = ap.parse_args(argv)
+    if args.profile:
+        return run_profile(args)
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)

@@ -179,8 +179,10 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
 cpb_status cpb_device_status(int* status);
 
 /* Test hook: mbarrier wait limit in polls (<= 0: default, about 1M polls) and
- * a row index whose copies are made to never complete (-1: off), applied to
- * subsequent launches of this process.  Used to exercise the timeout path. */
+ * a row index whose TMA copies are withheld (-1: off): its ring slot is told
+ * the row's byte count but no copy is issued, so the wait for that slot runs
+ * out and nothing is left in flight.  Applies to subsequent launches of this
+ * process.  Used to exercise the timeout path. */
 cpb_status cpb_debug_set(int wait_limit, int inject_row);
 
 /* FP64 sum of the field (CPB_F32: sum of (double)u; CPB_BF16_KAHAN: sum of

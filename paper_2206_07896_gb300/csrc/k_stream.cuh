@@ -58,7 +58,7 @@ struct StreamArgs {
   int depth;       // time steps of this pass, 1..K
   int stages;      // variant 1: ring slots per warp (power of two)
   int wait_limit;  // variant 1: bounded mbarrier wait, in try_wait polls
-  int inject_on;   // variant 1, tests only: 1 = the copies of row inject_row never complete
+  int inject_on;   // variant 1, tests only: 1 = the copies of row inject_row are never issued
   int inject_row;
 };
 
@@ -579,14 +579,15 @@ __device__ __forceinline__ CopyPlan make_copy_plan(const StreamArgs& a, int x0a,
 // (lane 0 posts the expected byte count; a complete_tx that lands before it is
 // allowed, the phase cannot finish before lane 0 arrives).  u and s are
 // skipped on a Dirichlet ghost row; kappa comes from the clamped row.
-// extra_bytes > 0 (tests only) expects bytes that never arrive.
+// withhold (tests only): post the byte count but issue none of the copies, so
+// the slot's phase never completes and no copy into it is in flight.
 template <bool BF>
 __device__ __forceinline__ void issue_row(const StreamArgs& a, const CopyPlan& cp, int r, int lane,
-                                          unsigned char* slot, uint64_t* bar, uint32_t extra_bytes) {
+                                          unsigned char* slot, uint64_t* bar, bool withhold) {
   const bool periodic = a.bc == BC_PERIODIC;
   const bool rin = periodic || (r >= 0 && r < a.ny);
-  if (lane == 0) mbar_arrive_expect_tx(bar, cp.kappa_bytes + (rin ? cp.us_bytes : 0u) + extra_bytes);
-  if (cp.active && (rin || cp.field == 0)) {
+  if (lane == 0) mbar_arrive_expect_tx(bar, cp.kappa_bytes + (rin ? cp.us_bytes : 0u));
+  if (cp.active && (rin || cp.field == 0) && !withhold) {
     const int rr = periodic ? wrap_near(r, a.ny) : clamp_index(r, a.ny);
     const size_t g = (size_t)rr * a.nx + cp.col;
     const size_t eb = cp.field == 1 ? Io<BF>::U_BYTES : Io<BF>::KS_BYTES;
@@ -676,7 +677,7 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
   __syncwarp();
   for (int i = 0; i < R && i < nrows; ++i)
     issue_row<BF>(a, cp, r_first + i, lane, ring + (size_t)i * SL::BYTES, &bars[i],
-                  (a.inject_on && r_first + i == a.inject_row) ? 16u : 0u);
+                  a.inject_on && r_first + i == a.inject_row);
   // Periodic refill cursor of this lane's copy: wrapped row and its source.
   const size_t row_bytes = (size_t)nx * (cp.field == 1 ? SL::UB : SL::KB);
   int next_row = 0;
@@ -719,8 +720,8 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
     const int slot = i & (R - 1);
     if (periodic) {
       const uint32_t bar = bars_s + 8u * slot;
-      if (lane == 0) mbar_arrive_expect_tx(bar, tx_periodic + (i == inject_i ? 16u : 0u));
-      if (cp.active) {
+      if (lane == 0) mbar_arrive_expect_tx(bar, tx_periodic);
+      if (cp.active && i != inject_i) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         bulk_g2s(ring_s + (uint32_t)(slot * SL::BYTES + cp.dst_off), next_src, cp.bytes, bar);
       }
@@ -731,7 +732,7 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
       }
     } else {
       issue_row<BF>(a, cp, r_first + i + R, lane, ring + (size_t)slot * SL::BYTES, &bars[slot],
-                    i == inject_i ? 16u : 0u);
+                    i == inject_i);
     }
   };
   // Advance the pipeline by input row i and store the finished row.
@@ -802,7 +803,7 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
   if (failed_at >= 0) {
     // Record the timeout, then give every row still in flight (issued but not
     // consumed) one more bounded wait so no copy targets this CTA's shared
-    // memory after it exits.
+    // memory after it exits (a withheld row has no copy in flight).
     if (lane == 0) atomicCAS(status, 0, (int)CPB_ERR_TIMEOUT);
     const int last = min(nrows, failed_at + R);
     for (int j = failed_at; j < last; ++j)

@@ -1,9 +1,10 @@
 """Failure detection without a GPU fault: a bounded device wait that runs out.
 
-The TMA-ring kernel waits on an mbarrier per row slot.  The test hook makes the
-copies of one row never complete (the barrier expects 16 bytes more than are
-issued), with a short wait limit: the kernel must record CPB_ERR_TIMEOUT in the
-device status word, drain its own copies and return; the context stays usable.
+The TMA-ring kernels wait on an mbarrier per row slot.  The test hook withholds
+the copies of one row (its slot's barrier is told the row's byte count, but no
+copy is issued, so the phase never completes), with a short wait limit: the
+kernel must record CPB_ERR_TIMEOUT in the device status word, drain its own
+copies and return; the context stays usable.
 """
 import numpy as np
 import pytest
@@ -24,10 +25,11 @@ def dev():
     return torch.device("cuda:0")
 
 
-@pytest.mark.parametrize("depth", [4, 8])   # single rows / rows in pairs
-def test_wait_timeout_is_reported_and_context_survives(dev, depth):
+@pytest.mark.parametrize("depth,bc", [(4, W.PERIODIC), (8, W.PERIODIC),   # single rows / rows in pairs
+                                      (4, W.DIRICHLET), (8, W.DIRICHLET)])
+def test_wait_timeout_is_reported_and_context_survives(dev, depth, bc):
     L = cpb.lib(fma=False)
-    g = W.random_grid(3, 256, 64, depth, W.PERIODIC)
+    g = W.random_grid(3, 256, 64, depth, bc)
     u = torch.from_numpy(g.u).to(dev)
     k = torch.from_numpy(g.kappa).to(dev)
     s = torch.from_numpy(g.src).to(dev)
