@@ -38,6 +38,17 @@
  *                   kappa, s: bf16 (uint16 bit patterns), nx*ny each.
  *                   Each step computes v in FP32 from the effective values,
  *                   then hi' = rn_bf16(v), cmp' = rn_bf16((float)hi' - v).
+ *   CPB_BF16_KAHAN_BLOCK  the same storage format; the steps of one pass of
+ *                   the temporal-blocked kernel (its depth k, see cpb_tuning)
+ *                   run in FP32 from the effective values, and only the
+ *                   result the pass stores is rounded into (hi, cmp) as
+ *                   above.  The result depends on the pass schedule: passes
+ *                   of depth k, a last pass of steps % k, and (with no
+ *                   scratch buffer) one pass of depth d >= 2 split into
+ *                   d - d/2 and d/2 when the pass count is even.  The
+ *                   reading of "BF16 storage, FP32 compute" in which storage
+ *                   happens where the kernel stores; CPB_BF16_KAHAN rounds
+ *                   every step as if each were stored.
  * Streams are CUDA stream handles (cudaStream_t); NULL is the legacy default
  * stream.
  *
@@ -68,7 +79,7 @@ typedef enum {
   CPB_ERR_WORKSPACE = 7           /* workspace missing or smaller than required        */
 } cpb_status;
 
-typedef enum { CPB_F32 = 0, CPB_BF16_KAHAN = 1 } cpb_dtype;
+typedef enum { CPB_F32 = 0, CPB_BF16_KAHAN = 1, CPB_BF16_KAHAN_BLOCK = 2 } cpb_dtype;
 typedef enum { CPB_DIRICHLET0 = 0, CPB_PERIODIC = 1 } cpb_boundary;
 
 typedef struct {

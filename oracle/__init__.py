@@ -15,7 +15,10 @@ Functions (all numpy in, numpy out):
                                       and coarse-grained fetching (Sec. IV), and
                                       inside each block one thread loop per
                                       barrier-free region (Sec. III "SPMD to MPMD").
-* ``direct_bf16k``                    BF16-Kahan storage, FP32 compute.
+* ``direct_bf16k``                    BF16-Kahan storage, FP32 compute, every step
+                                      rounded into storage.
+* ``direct_bf16k_block``              BF16-Kahan storage rounded once per pass of
+                                      a temporal-block schedule (``pass_schedule``).
 * ``sample``                          sampled cells of a large run via their
                                       dependency cones (bit-identical to ``direct``).
 * ``heat_sum_*``                      FP64 sums.
@@ -236,6 +239,37 @@ def direct_bf16k(state, kappa_bf16, src_bf16, steps, dt, bc, pool=1, compensate=
                                   _c(src_bf16, np.uint16), nx, ny, steps, float(np.float32(dt)), bc,
                                   1 if compensate else 0, pool, out), "direct_bf16k")
     return out
+
+
+def pass_schedule(steps, k, have_scratch=True):
+    """Depths of the passes the library runs for `steps` steps at depth k: k
+    each, then steps % k; without a scratch buffer an even pass count is made
+    odd by splitting the last pass of depth >= 2 into d - d//2 and d//2 (the
+    rule the C header states for CPB_BF16_KAHAN_BLOCK).  Host logic only: the
+    input of direct_bf16k_block."""
+    d = [k] * (steps // k) + ([steps % k] if steps % k else [])
+    if not have_scratch and d and len(d) % 2 == 0:
+        for i in range(len(d) - 1, -1, -1):
+            if d[i] >= 2:
+                d[i:i + 1] = [d[i] - d[i] // 2, d[i] // 2]
+                break
+    return d
+
+
+def direct_bf16k_block(state, kappa_bf16, src_bf16, depths, dt, bc, pool=1):
+    """BF16-Kahan storage rounded once per pass: for each pass depth d the
+    state's value hi - cmp (exact in FP32) advances d steps of the FP32 direct
+    update with the bf16 kappa and source widened to FP32, then is rounded back
+    into (hi, cmp) = (rn(v), rn(hi - v)).  Composed of direct() and
+    bf16k_pack(), both pinned on their own."""
+    st = np.ascontiguousarray(state, dtype=np.uint32)
+    k32 = bf16_to_f32(kappa_bf16).reshape(st.shape)
+    s32 = bf16_to_f32(src_bf16).reshape(st.shape)
+    for d in depths:
+        u = bf16k_value(st).astype(np.float32)
+        u = direct(u, k32, s32, int(d), dt, bc, "f32", pool=pool)
+        st = bf16k_pack(u)
+    return st
 
 
 def heat_sum_f32(u) -> float:

@@ -32,6 +32,7 @@ CPB_ERR_WORKSPACE = 7
 
 CPB_F32 = 0
 CPB_BF16_KAHAN = 1
+CPB_BF16_KAHAN_BLOCK = 2
 CPB_DIRICHLET0 = 0
 CPB_PERIODIC = 1
 

@@ -44,6 +44,7 @@ bool aligned(const void* p, size_t a) { return p == nullptr || (reinterpret_cast
 
 size_t u_bytes(cpb_dtype) { return 4; }                    // f32 or (hi, cmp) word
 size_t ks_bytes(cpb_dtype d) { return d == CPB_F32 ? 4 : 2; }  // kappa / source element
+bool dtype_ok(int d) { return d == CPB_F32 || d == CPB_BF16_KAHAN || d == CPB_BF16_KAHAN_BLOCK; }
 
 bool overlap(const void* a, const void* b, size_t n) {
   if (!a || !b) return false;
@@ -77,7 +78,7 @@ bool tuning_valid(const cpb_tuning& t) {
 
 // Variant 1 (TMA bulk-copy ring) needs aligned rows; otherwise variant 0 runs.
 bool bulk_eligible(int nx, cpb_dtype d, bool vec, const void* kappa, const void* src) {
-  const bool bf = d == CPB_BF16_KAHAN;
+  const bool bf = d != CPB_F32;
   return vec && nx % bulk_align_cells(bf) == 0 && nx >= bulk_slot_cells(bf) && aligned(kappa, 16) &&
          aligned(src, 16);
 }
@@ -154,7 +155,7 @@ cpb_status check_common(const Fields& f, int nx, int ny, int steps, float dt, cp
   if (nx < 1 || ny < 1 || steps < 0) return CPB_ERR_INVALID_VALUE;
   if (!(dt > 0.0f) || !std::isfinite(dt)) return CPB_ERR_INVALID_VALUE;
   if (bc != CPB_DIRICHLET0 && bc != CPB_PERIODIC) return CPB_ERR_INVALID_VALUE;
-  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  if (!dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
   if (!f.u_in || !f.u_out || !f.kappa) return CPB_ERR_INVALID_VALUE;
   const size_t n = (size_t)nx * (size_t)ny;
   if (n > (size_t)1 << 40) return CPB_ERR_INVALID_VALUE;
@@ -214,7 +215,9 @@ cpb_status enqueue_tuned(const Fields& f, int nx, int ny, int steps, float dt, c
     p.u_in = src_buf;
     p.u_out = dst;
     p.depth = depths[i];
-    cudaError_t e = dtype == CPB_F32 ? launch_stream_f32(p, t.k, s) : launch_stream_bf16k(p, t.k, s);
+    cudaError_t e = dtype == CPB_F32          ? launch_stream_f32(p, t.k, s)
+                    : dtype == CPB_BF16_KAHAN ? launch_stream_bf16k(p, t.k, s)
+                                              : launch_stream_bf16k_block(p, t.k, s);
     CPB_TRY(e);
     src_buf = dst;
   }
@@ -526,7 +529,7 @@ cpb_status cpb_tuning_load(const char* path, const char* device, int* loaded) {
     char tail = 0;
     const int got = std::sscanf(line, "cpb-tuning %d %255s %d %d %d %d %d %d %d %d %d %c", &ver, name, &nx, &ny,
                                 &dt, &bc, &t.k, &t.chunk_rows, &t.warps_per_block, &t.variant, &t.stages, &tail);
-    if (got != 11 || ver != 1 || nx < 1 || ny < 1 || (dt != CPB_F32 && dt != CPB_BF16_KAHAN) ||
+    if (got != 11 || ver != 1 || nx < 1 || ny < 1 || !dtype_ok(dt) ||
         (bc != CPB_DIRICHLET0 && bc != CPB_PERIODIC) || !tuning_valid(t)) {
       g_last_error = std::string("bad tuning line: ") + line;
       st = CPB_ERR_INVALID_VALUE;
@@ -611,10 +614,11 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
 cpb_status cpb_device_status(int* status) {
   if (!status) return CPB_ERR_INVALID_VALUE;
   CPB_TRY(cudaDeviceSynchronize());
-  int a = 0, b = 0;
+  int a = 0, b = 0, c = 0;
   CPB_TRY(read_stream_status_f32(&a));
   CPB_TRY(read_stream_status_bf16k(&b));
-  *status = a ? a : b;
+  CPB_TRY(read_stream_status_bf16k_block(&c));
+  *status = a ? a : (b ? b : c);
   return CPB_SUCCESS;
 }
 
@@ -633,7 +637,7 @@ size_t cpb_heat_sum_workspace_bytes(int nx, int ny) {
 cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
                         void* workspace, size_t ws_bytes, cpb_stream_t stream) {
   if (!u || !d_out || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
-  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  if (!dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
   if (!aligned(u, 4) || !aligned(d_out, 8)) return CPB_ERR_INVALID_VALUE;
   const long long n = (long long)nx * ny;
   const int nb = heat_sum_blocks(n);
@@ -646,7 +650,7 @@ cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* 
 cpb_status cpb_heat_sum_noalloc(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
                                 cpb_stream_t stream) {
   if (!u || !d_out || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
-  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  if (!dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
   if (!aligned(u, 4) || !aligned(d_out, 8)) return CPB_ERR_INVALID_VALUE;
   const long long n = (long long)nx * ny;
   if (n > heat_sum_noalloc_max_cells()) {
@@ -687,7 +691,7 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
                             cpb_dtype dtype, void* d_workspace, size_t ws_bytes,
                             cpb_stream_t stream) {
   if (!u0_host || !kappa_host || !u_out_host || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
-  if (dtype != CPB_F32 && dtype != CPB_BF16_KAHAN) return CPB_ERR_INVALID_VALUE;
+  if (!dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
   const size_t need = cpb_host_workspace_bytes(nx, ny, dtype);
   if (!d_workspace || ws_bytes < need || !aligned(d_workspace, 256)) return CPB_ERR_WORKSPACE;
   const size_t n = (size_t)nx * ny;

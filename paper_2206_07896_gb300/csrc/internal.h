@@ -56,9 +56,11 @@ inline size_t stream_smem_bytes(bool bf16, int k, int warps, int variant, int st
 // One pass of instantiated depth k (1..8) over the whole grid.
 cudaError_t launch_stream_f32(const StreamPass& p, int k, cudaStream_t s);
 cudaError_t launch_stream_bf16k(const StreamPass& p, int k, cudaStream_t s);
-// Read and clear the device status word of the f32 / bf16 stream kernels.
+cudaError_t launch_stream_bf16k_block(const StreamPass& p, int k, cudaStream_t s);
+// Read and clear the device status word of the f32 / bf16 / bf16-block stream kernels.
 cudaError_t read_stream_status_f32(int* out);
 cudaError_t read_stream_status_bf16k(int* out);
+cudaError_t read_stream_status_bf16k_block(int* out);
 
 // The shared-memory temporal-blocked tiled kernel (k_tile.cu): d steps per
 // launch, bx x by threads, four (bx + 2d) x (by + 2d) float tiles.

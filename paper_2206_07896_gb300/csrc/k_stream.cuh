@@ -36,9 +36,11 @@
 //
 // Storage
 //   F32: u, kappa, s float.  BF16-Kahan: u as (hi | cmp << 16) words, kappa and
-//   s bf16; every level rounds its result into (hi, cmp) and continues from the
-//   represented value hi - cmp, exactly as if each step were stored.  A null
-//   source pointer means s = 0.
+//   s bf16.  RE = true (CPB_BF16_KAHAN): every level rounds its result into
+//   (hi, cmp) and continues from the represented value hi - cmp, exactly as if
+//   each step were stored.  RE = false (CPB_BF16_KAHAN_BLOCK): the levels of a
+//   pass run in FP32 and only the row a pass stores is rounded into (hi, cmp).
+//   A null source pointer means s = 0.
 #pragma once
 
 #include "common.cuh"
@@ -236,7 +238,7 @@ __device__ __forceinline__ float2 kahan_round2(float2 v, uint2& words) {
 // Registers: U[t][p] holds level t's row written at iteration parity p (t = 0
 // is the input), G[t][p] level t+1's north fluxes; with the row loop unrolled
 // by 2 every index is a compile-time constant and no copies are needed.
-template <int K, bool BF>
+template <int K, bool BF, bool RE = true>
 struct Pipe {
   float4 U[K][2];
   float4 G[K][2];
@@ -309,11 +311,16 @@ struct Pipe {
         const float2 acch = add2(hi2(hsum), sub2(gh, hi2(Gb)));
         float4 v = cat4(add2(lo2(C), madd2(h2, accl, lo2(ds))), add2(hi2(C), madd2(h2, acch, hi2(ds))));
         uint4 pk = make_uint4(0, 0, 0, 0);
-        if (BF) {
+        if (BF && RE) {  // round every level into storage and continue from the stored value
           uint2 wl, wh;
           const float2 el = kahan_round2(lo2(v), wl), eh = kahan_round2(hi2(v), wh);
           pk = make_uint4(wl.x, wl.y, wh.x, wh.y);
           v = cat4(el, eh);
+        } else if (BF && (FULL ? t == K : t == d)) {  // round only the row the pass stores
+          uint2 wl, wh;
+          kahan_round2(lo2(v), wl);
+          kahan_round2(hi2(v), wh);
+          pk = make_uint4(wl.x, wl.y, wh.x, wh.y);
         }
         if (!periodic) {  // Dirichlet ghosts stay at zero
           if (rho < 0 || rho >= ny) v = f4(0.0f);
@@ -366,7 +373,7 @@ __device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int n
 // wrote earlier (the batched persistent kernel); otherwise the read-only path.
 // FULL: the pass depth is K (known at compile time, so the per-level depth
 // guards fold away); otherwise the depth a.depth <= K is read at run time.
-template <int K, bool BF, bool COH, bool FULL = false>
+template <int K, bool BF, bool COH, bool FULL = false, bool RE = true>
 __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int lane, float4* face_ring) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
@@ -414,7 +421,7 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
     }
   };
 
-  Pipe<K, BF> pipe;
+  Pipe<K, BF, RE> pipe;
   pipe.init(face_ring, lane);
   const int r_end = y1 + d;
   float4 pu, pk, ps;
@@ -437,7 +444,7 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
   if (r_in < r_end) body(Int<0>{}, r_in);
 }
 
-template <int K, bool BF>
+template <int K, bool BF, bool RE>
 __global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int wib = threadIdx.x >> 5;
@@ -445,9 +452,9 @@ __global__ void __launch_bounds__(256) stream_kernel(const StreamArgs a) {
   if (item >= a.n_items) return;  // warp-uniform
   float4* face = reinterpret_cast<float4*>(smem + (size_t)wib * face_ring_rows(K) * FACE_SLOT_BYTES);
   if (a.depth == K)
-    stream_item<K, BF, false, true>(a, item, threadIdx.x & 31, face);
+    stream_item<K, BF, false, true, RE>(a, item, threadIdx.x & 31, face);
   else
-    stream_item<K, BF, false, false>(a, item, threadIdx.x & 31, face);
+    stream_item<K, BF, false, false, RE>(a, item, threadIdx.x & 31, face);
 }
 
 // ---------------------------------------------------------------------------
@@ -639,7 +646,7 @@ __host__ __device__ constexpr bool rows_in_pairs(int k) { return k >= 6; }
 // the same body with run-time face slots.  Periodic refills walk a per-lane
 // source pointer row by row (one compare for the wrap) and expect a constant
 // byte count; Dirichlet refills go through issue_row (ghost rows).
-template <int K, bool BF, bool FULL, bool PERIODIC, bool LV>
+template <int K, bool BF, bool FULL, bool PERIODIC, bool LV, bool RE>
 __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int lane, unsigned char* ring,
                                              uint64_t* bars, float4* face, int* status, const LevelOut* lv) {
   constexpr int HALO = (K + 3) & ~3;
@@ -688,7 +695,7 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
   }
   const uint32_t tx_periodic = cp.kappa_bytes + cp.us_bytes;
 
-  Pipe<K, BF> pipe;
+  Pipe<K, BF, RE> pipe;
   pipe.init(face, lane);
   int failed_at = -1;
   // Wait for input row i (slot i mod R) and read the lane's kappa, u and s.
@@ -819,13 +826,13 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
   return true;
 }
 
-template <int K, bool BF, bool FULL, bool LV = false>
+template <int K, bool BF, bool FULL, bool LV = false, bool RE = true>
 __device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lane, unsigned char* ring,
                                           uint64_t* bars, float4* face, int* status,
                                           const LevelOut* lv = nullptr) {
   if (a.bc == BC_PERIODIC)
-    return bulk_item_bc<K, BF, FULL, true, LV>(a, item, lane, ring, bars, face, status, lv);
-  return bulk_item_bc<K, BF, FULL, false, LV>(a, item, lane, ring, bars, face, status, lv);
+    return bulk_item_bc<K, BF, FULL, true, LV, RE>(a, item, lane, ring, bars, face, status, lv);
+  return bulk_item_bc<K, BF, FULL, false, LV, RE>(a, item, lane, ring, bars, face, status, lv);
 }
 
 // Shared memory of a CTA of `nwarps` warps using the row ring:
@@ -845,7 +852,7 @@ struct BulkSmem {
   }
 };
 
-template <int K, bool BF>
+template <int K, bool BF, bool RE>
 __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -853,9 +860,9 @@ __global__ void __launch_bounds__(256) stream_bulk_kernel(const StreamArgs a) {
   if (item >= a.n_items) return;  // warp-uniform; no block-level barrier is used
   const BulkSmem<K, BF> sm(smem, wib, nwarps, a.stages);
   if (a.depth == K)
-    bulk_item<K, BF, true>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status);
+    bulk_item<K, BF, true, false, RE>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status);
   else
-    bulk_item<K, BF, false>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status);
+    bulk_item<K, BF, false, false, RE>(a, item, threadIdx.x & 31, sm.ring, sm.bars, sm.face, &g_stream_status);
 }
 
 // The same pass, also storing the rows of every intermediate level, so that a
@@ -879,10 +886,11 @@ __global__ void __launch_bounds__(256) stream_bulk_levels_kernel(const StreamArg
 // ---------------------------------------------------------------------------
 namespace {
 // Per (variant, storage, depth) kernel: devices (bit per ordinal < 32) on which
-// the shared-memory opt-in was set.  Internal linkage: one per translation
+// the shared-memory opt-in was set.  Storage: 0 FP32, 1 BF16-Kahan rounded
+// every level, 2 BF16-Kahan rounded where stored.  Internal linkage: one per translation
 // unit and library (a function-local static of a template would be merged
 // across every shared object loaded in the process).
-unsigned g_smem_attr_done[2][2][9];
+unsigned g_smem_attr_done[2][3][9];
 unsigned g_smem_attr_levels_done;  // the level-storing kernel (depth 4, FP32)
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory, once per device.
@@ -906,7 +914,7 @@ inline cudaError_t ensure_smem_optin(const void* fn, unsigned& done, size_t shm)
 }
 }  // namespace
 
-template <int K, bool BF>
+template <int K, bool BF, bool RE>
 cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
@@ -952,29 +960,29 @@ cudaError_t launch_stream_k(const StreamPass& p, cudaStream_t s) {
       return cudaErrorInvalidValue;
     }
   }
-  cudaError_t e = ensure_smem_optin(bulk ? (const void*)stream_bulk_kernel<K, BF>
-                                         : (const void*)stream_kernel<K, BF>,
-                                    g_smem_attr_done[bulk ? 1 : 0][BF ? 1 : 0][K], shm);
+  cudaError_t e = ensure_smem_optin(bulk ? (const void*)stream_bulk_kernel<K, BF, RE>
+                                         : (const void*)stream_kernel<K, BF, RE>,
+                                    g_smem_attr_done[bulk ? 1 : 0][BF ? (RE ? 1 : 2) : 0][K], shm);
   if (e != cudaSuccess) return e;
   (void)cudaGetLastError();  // drop a stale non-sticky error so the check below is this launch's
   if (bulk)
-    stream_bulk_kernel<K, BF><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
+    stream_bulk_kernel<K, BF, RE><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
   else
-    stream_kernel<K, BF><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
+    stream_kernel<K, BF, RE><<<(unsigned)blocks, 32 * wpb, shm, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool BF>
+template <bool BF, bool RE = true>
 cudaError_t launch_stream_any(const StreamPass& p, int k, cudaStream_t s) {
   switch (k) {
-    case 1: return launch_stream_k<1, BF>(p, s);
-    case 2: return launch_stream_k<2, BF>(p, s);
-    case 3: return launch_stream_k<3, BF>(p, s);
-    case 4: return launch_stream_k<4, BF>(p, s);
-    case 5: return launch_stream_k<5, BF>(p, s);
-    case 6: return launch_stream_k<6, BF>(p, s);
-    case 7: return launch_stream_k<7, BF>(p, s);
-    case 8: return launch_stream_k<8, BF>(p, s);
+    case 1: return launch_stream_k<1, BF, RE>(p, s);
+    case 2: return launch_stream_k<2, BF, RE>(p, s);
+    case 3: return launch_stream_k<3, BF, RE>(p, s);
+    case 4: return launch_stream_k<4, BF, RE>(p, s);
+    case 5: return launch_stream_k<5, BF, RE>(p, s);
+    case 6: return launch_stream_k<6, BF, RE>(p, s);
+    case 7: return launch_stream_k<7, BF, RE>(p, s);
+    case 8: return launch_stream_k<8, BF, RE>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }

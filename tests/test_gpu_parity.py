@@ -178,6 +178,30 @@ def test_bf16k_bit_exact(dev, exact, bc, k):
             np.testing.assert_array_equal(got.view(np.uint32), ref)
 
 
+@pytest.mark.parametrize("bc", [D, P])
+@pytest.mark.parametrize("k", [1, 2, 4, 6, 8])
+def test_bf16k_block_bit_exact(dev, exact, bc, k):
+    # BF16-Kahan storage rounded only where a pass stores: both row-load
+    # variants, both scratch modes (the pass schedule differs), ragged sizes.
+    for (nx, ny) in [(272, 70), (300, 45), (136, 50), (6, 5), (1088, 33)]:
+        for steps in (2 * k + 1, 4 * k):
+            g = W.random_grid(nx + 3 * ny + k, nx, ny, steps, bc)
+            st = oracle.bf16k_pack(g.u)
+            kb, sb = oracle.bf16_round(g.kappa), oracle.bf16_round(g.src)
+            fields = (to_dev(st.view(np.int32), dev), to_dev(kb.view(np.int16), dev),
+                      to_dev(sb.view(np.int16), dev))
+            for variant, stages in ((0, 2), (1, 2), (1, 8)):
+                for scratch in (True, False):
+                    ref = oracle.direct_bf16k_block(st, kb, sb, oracle.pass_schedule(steps, k, scratch),
+                                                    g.dt, bc)
+                    got = run_tuned(exact, g, dev, {"k": k, "chunk_rows": 24, "warps_per_block": 2,
+                                                    "variant": variant, "stages": stages},
+                                    dtype=cpb.CPB_BF16_KAHAN_BLOCK, fields=fields, scratch=scratch)
+                    np.testing.assert_array_equal(got.view(np.uint32), ref,
+                                                  err_msg=f"{nx}x{ny} steps={steps} v{variant} scratch={scratch}")
+    assert exact.cpb_device_status() == 0
+
+
 def test_bf16_conversions_match_oracle(dev, exact):
     x = np.random.default_rng(4).standard_normal(100003).astype(np.float32)
     xd = to_dev(x, dev)

@@ -4,7 +4,9 @@
   after 1000 steps on the 8192^2 periodic workload, and after 2000 steps on the
   precision workload's distributions.
 * BF16-Kahan storage within 1e-2 of FP64 (error reported both against the
-  original FP32 inputs and against the bf16-quantised inputs).
+  original FP32 inputs and against the bf16-quantised inputs), on a 1024^2
+  grid and on the full 16384^2 precision workload (2000 steps, both rounding
+  readings, the autotuned configurations).
 * Full-size launches in the benchmark's configuration: sampled cells equal the
   oracle's dependency-cone values bit for bit (--fmad=false build).
 * Heat conservation at full size (periodic, s = 0) with the FP64 heat sum.
@@ -90,6 +92,72 @@ def test_fp32_and_bf16k_precision_distributions_2000_steps(dev):
     assert e32 <= 1e-5
     assert e16 <= 1e-2
     assert e16q <= 1e-3
+
+
+def _bf16_fields(L, dev, g):
+    N = g.nx * g.ny
+    u, k, s = (torch.from_numpy(x).to(dev) for x in (g.u, g.kappa, g.src))
+    st = torch.empty(N, dtype=torch.int32, device=dev)
+    kb = torch.empty(N, dtype=torch.int16, device=dev)
+    sb = torch.empty(N, dtype=torch.int16, device=dev)
+    L.cpb_bf16k_pack(u, st, N)
+    L.cpb_bf16_round(k, kb, N)
+    L.cpb_bf16_round(s, sb, N)
+    return st, kb, sb
+
+
+def _run_tuned_dtype(L, dev, g, fields, dtype):
+    """Autotune on copies (as the benchmark does), then the whole run."""
+    u, k, s = fields
+    a, b = torch.empty_like(u), torch.empty_like(u)
+    a.copy_(u)
+    t = L.cpb_autotune(a, b, k, s, g.nx, g.ny, 24, float(g.dt), g.bc, dtype)
+    out = torch.empty_like(u)
+    L.cpb_stencil_launch_tuned(u, out, k, s, g.nx, g.ny, g.steps, float(g.dt), g.bc, dtype, tuning=t,
+                               scratch=a)
+    torch.cuda.synchronize()
+    del a, b
+    return out.cpu().numpy(), t
+
+
+@pytest.mark.slow
+def test_precision_workload_full_size_against_fp64(dev):
+    # The precision workload as stated: 16384^2, Dirichlet, 2000 steps, at the
+    # autotuned configurations the benchmark times.  FP32 within 1e-5 and
+    # BF16-Kahan storage (both rounding readings) within 1e-2 relative L-inf
+    # of the FP64 oracle on the original FP32 inputs; the BF16 forms also
+    # against FP64 on the bf16-quantised inputs (the storage error alone).
+    g = W.precision()
+    pool = oracle.host_cores()
+    L = cpb.lib(fma=True)
+    shape = (g.ny, g.nx)
+    f32 = tuple(torch.from_numpy(x).to(dev) for x in (g.u, g.kappa, g.src))
+    got32, t32 = _run_tuned_dtype(L, dev, g, f32, cpb.CPB_F32)
+    del f32
+    bf = _bf16_fields(L, dev, g)
+    got16, t16 = _run_tuned_dtype(L, dev, g, bf, cpb.CPB_BF16_KAHAN)
+    got16b, t16b = _run_tuned_dtype(L, dev, g, bf, cpb.CPB_BF16_KAHAN_BLOCK)
+    st0, kb, sb = (x.cpu().numpy() for x in bf)
+    del bf
+    torch.cuda.empty_cache()
+    v16 = oracle.bf16k_value(got16.view(np.uint32)).reshape(shape)
+    v16b = oracle.bf16k_value(got16b.view(np.uint32)).reshape(shape)
+    del got16, got16b
+    ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, g.bc, "f64", pool=pool)
+    e32, e16, e16b = rel_linf(got32.reshape(shape), ref), rel_linf(v16, ref), rel_linf(v16b, ref)
+    del ref, got32
+    kq = oracle.bf16_to_f32(kb.view(np.uint16)).reshape(shape)
+    sq = oracle.bf16_to_f32(sb.view(np.uint16)).reshape(shape)
+    u0q = oracle.bf16k_value(st0.view(np.uint32)).reshape(shape)
+    del g.u, g.kappa, g.src
+    refq = oracle.direct(u0q, kq, sq, g.steps, g.dt, g.bc, "f64", pool=pool)
+    e16q, e16bq = rel_linf(v16, refq), rel_linf(v16b, refq)
+    print(f"precision 16384^2 x 2000 rel L-inf vs FP64: FP32 {e32:.3e} (depth {t32['k']}), "
+          f"BF16-Kahan every step {e16:.3e} (quantised inputs {e16q:.3e}, depth {t16['k']}), "
+          f"BF16-Kahan per pass {e16b:.3e} (quantised inputs {e16bq:.3e}, depth {t16b['k']})")
+    assert e32 <= 1e-5
+    assert e16 <= 1e-2 and e16b <= 1e-2
+    assert e16q <= 1e-3 and e16bq <= 1e-3
 
 
 @pytest.mark.parametrize("which", ["plain_scale", "precision"])

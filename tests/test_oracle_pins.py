@@ -283,6 +283,43 @@ def test_bf16k_pool_equals_serial():
     np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("bc", [D, P])
+def test_bf16k_block_with_depth_one_passes_is_per_step_rounding(bc):
+    # Rounding once per pass with passes of one step is rounding every step:
+    # the Python composition (FP32 loop + pack) equals the C++ BF16-Kahan loop.
+    for seed, nx, ny, steps in ((5, 70, 33, 11), (6, 9, 130, 7), (7, 1, 1, 3)):
+        g, st, kb, sb = _bf16_case(seed, nx, ny, steps, bc)
+        a = oracle.direct_bf16k(st, kb, sb, steps, g.dt, bc)
+        b = oracle.direct_bf16k_block(st, kb, sb, [1] * steps, g.dt, bc)
+        np.testing.assert_array_equal(a, b)
+
+
+def test_bf16k_block_accuracy():
+    # Rounded once per pass of 8 steps, the storage error against FP64 on the
+    # bf16-quantised inputs is no larger than with every step rounded.
+    g, st, kb, sb = _bf16_case(3, 96, 80, 800, D)
+    k64, s64 = oracle.bf16_to_f32(kb).astype(np.float64), oracle.bf16_to_f32(sb).astype(np.float64)
+    ref = oracle.direct(oracle.bf16k_value(st), k64, s64, g.steps, g.dt, D, "f64")
+    every = oracle.bf16k_value(oracle.direct_bf16k(st, kb, sb, g.steps, g.dt, D))
+    block = oracle.bf16k_value(oracle.direct_bf16k_block(st, kb, sb, oracle.pass_schedule(g.steps, 8), g.dt, D))
+    err_e = np.max(np.abs(every - ref)) / np.max(np.abs(ref))
+    err_b = np.max(np.abs(block - ref)) / np.max(np.abs(ref))
+    assert err_b <= err_e and err_b <= 1e-3
+
+
+def test_pass_schedule():
+    for steps in range(0, 40):
+        for k in range(1, 9):
+            for scratch in (True, False):
+                d = oracle.pass_schedule(steps, k, scratch)
+                assert sum(d) == steps and all(1 <= x <= k for x in d)
+                if not scratch and any(x >= 2 for x in d):
+                    assert len(d) % 2 == 1
+    assert oracle.pass_schedule(17, 4) == [4, 4, 4, 4, 1]
+    assert oracle.pass_schedule(16, 4, False) == [4, 4, 4, 2, 2]
+    assert oracle.pass_schedule(9, 4, False) == [4, 4, 1]
+
+
 def test_bf16k_pack_represents_float_closely():
     u = np.random.default_rng(1).random(10000, dtype=np.float32)
     v = oracle.bf16k_value(oracle.bf16k_pack(u))
@@ -328,6 +365,31 @@ def test_adjoint_against_central_differences(bc):
         assert abs(fd - gd) <= 1e-6 * abs(gd) + 1e-10
         fd = (_loss(u0, k + eps * d, s, tgt, steps, g.dt, bc)
               - _loss(u0, k - eps * d, s, tgt, steps, g.dt, bc)) / (2 * eps)
+        gd = float(np.sum(gk * d))
+        assert abs(fd - gd) <= 1e-6 * abs(gd) + 1e-10
+
+
+def test_adjoint_64_directions_on_the_differentiation_schedule():
+    # The differentiation workload's schedule and fields (Dirichlet, kappa ~
+    # U[0.5, 1), u0 ~ U[0, 1), no source, r = 0.2, 200 steps, checkpoints every
+    # 20, target = 8 seeded sinusoids) on a 128 x 128 grid: the FP64 adjoint
+    # against FP64 central differences (eps = 1e-3) on 64 seeded unit
+    # directions each for u0 and kappa.
+    g = W.differentiation(seed=4, n=128, steps=200, ckpt=20)
+    u0, k = g.u.astype(np.float64), g.kappa.astype(np.float64)
+    s = np.zeros_like(u0)
+    tgt = g.extras["target"].astype(np.float64)
+    steps, ckpt, dt = g.steps, g.extras["ckpt"], float(g.dt)
+    L, gu, gk = oracle.adjoint_f64(u0, k, s, tgt, steps, dt, g.bc, ckpt, pool=4)
+    assert abs(L - _loss(u0, k, s, tgt, steps, dt, g.bc)) <= 1e-12 * L
+    eps = 1e-3
+    for d in W.unit_directions(40, 64, u0.shape):
+        fd = (_loss(u0 + eps * d, k, s, tgt, steps, dt, g.bc)
+              - _loss(u0 - eps * d, k, s, tgt, steps, dt, g.bc)) / (2 * eps)
+        gd = float(np.sum(gu * d))
+        assert abs(fd - gd) <= 1e-6 * abs(gd) + 1e-10
+        fd = (_loss(u0, k + eps * d, s, tgt, steps, dt, g.bc)
+              - _loss(u0, k - eps * d, s, tgt, steps, dt, g.bc)) / (2 * eps)
         gd = float(np.sum(gk * d))
         assert abs(fd - gd) <= 1e-6 * abs(gd) + 1e-10
 
