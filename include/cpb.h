@@ -215,12 +215,18 @@ cpb_status cpb_heat_sum(const void* u, int nx, int ny, cpb_dtype dtype, double* 
  * The per-block partial sums live in a 32 KB array inside the library (one
  * per GPU that loads it, held until the process exits).  Grids of more than
  * 2^26 cells (67,108,864) are rejected with CPB_ERR_WORKSPACE before any
- * launch; use cpb_heat_sum for those.  The call allocates nothing.  Its
- * first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the array: calls whose executions overlap on the
- * GPU (unordered streams) race and may return wrong sums.  The blocking
- * differs from cpb_heat_sum, so the two may differ in the last bits. */
+ * launch; use cpb_heat_sum for those.  The call allocates nothing.  Every
+ * call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress: no allocation, no synchronisation), so the address
+ * stays right across a cudaDeviceReset; the first call on a device may load
+ * the library's device code, so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's partial
+ * sums; every partial a call reads it has written itself, so nothing needs
+ * clearing.  Calls whose executions overlap on the GPU (unordered streams)
+ * race on the array and may return wrong sums: order them on one stream.
+ * The blocking differs from cpb_heat_sum, so the two may differ in the last
+ * bits when the sum is not exact in FP64 (it is exact, and the two equal,
+ * for FP32 values that are multiples of 2^-24 in [0, 1)). */
 cpb_status cpb_heat_sum_noalloc(const void* u, int nx, int ny, cpb_dtype dtype, double* d_out,
                                 cpb_stream_t stream);
 

@@ -6,7 +6,6 @@
 // tree, block tree, then one block over the per-block partials), so the same
 // input gives the same bits on the same device.  This is the only FP64
 // arithmetic on the GPU path.
-#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -170,24 +169,16 @@ constexpr long long NOALLOC_CELLS_PER_BLOCK = 16384;
 static __device__ __align__(256) double g_heat_sum_scratch[NOALLOC_MAX_PARTIALS];
 
 namespace {
-std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[64];  // device address of g_heat_sum_scratch, per device ordinal
-
-// Set-up, once per device, with that device current: the host-side name of a
-// __device__ array is not a device address, so ask the runtime for it.
+// The host-side name of a __device__ array is not a device address: ask the
+// runtime for it, with the device current, on every call.  The lookup
+// allocates nothing and does not synchronise; asking each time (instead of
+// caching per device) keeps the address right after a cudaDeviceReset, which
+// reloads the module at a new address.
 cudaError_t noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_heat_sum_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_heat_sum_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 }  // namespace
