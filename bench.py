@@ -287,6 +287,15 @@ def form_precision(L, cpb, dev, stream, n=16384, steps=2000):
     L.cpb_bf16k_unpack(so, un, N, stream=sh)
     torch.cuda.synchronize()
     diff = float((un - ref32).abs().max() / ref32.abs().max())
+    # BF16-Kahan storage rounded once per pass (CPB_BF16_KAHAN_BLOCK)
+    sa.copy_(st)
+    t16b = L.cpb_autotune(sa, sbuf, kb, sb, nx, ny, 24, dt, W.DIRICHLET, cpb.CPB_BF16_KAHAN_BLOCK, stream=sh)
+    ms16b = _time(lambda: L.cpb_stencil_launch_tuned(st, so, kb, sb, nx, ny, steps, dt, W.DIRICHLET,
+                                                     cpb.CPB_BF16_KAHAN_BLOCK, tuning=t16b, scratch=sa,
+                                                     stream=sh), 2, stream)
+    L.cpb_bf16k_unpack(so, un, N, stream=sh)
+    torch.cuda.synchronize()
+    diff_b = float((un - ref32).abs().max() / ref32.abs().max())
     upd = N * steps
     hbm, _ = peaks()
     # The same comparison at depth 2, where both storages are HBM-bound (the
@@ -303,12 +312,18 @@ def form_precision(L, cpb, dev, stream, n=16384, steps=2000):
                     "effective_gbs_16B": upd * 16 / t32["k"] / ms32 / 1e6},
             "bf16_kahan": {"gcells": upd / ms16 / 1e6, "ms": ms16, "tuning": t16,
                            "effective_gbs_12B": upd * 12 / t16["k"] / ms16 / 1e6,
-                           "rel_linf_vs_f32_gpu": diff},
+                           "rel_linf_vs_f32_gpu": diff, "rounding": "every step"},
+            "bf16_kahan_block": {"gcells": upd / ms16b / 1e6, "ms": ms16b, "tuning": t16b,
+                                 "effective_gbs_12B": upd * 12 / t16b["k"] / ms16b / 1e6,
+                                 "rel_linf_vs_f32_gpu": diff_b, "rounding": "once per pass (where stored)"},
             "speedup_bf16_vs_f32": ms32 / ms16,
+            "speedup_bf16_block_vs_f32": ms32 / ms16b,
             "at_depth_2": {"f32_gcells": upd / ms32_k2 / 1e6, "bf16_kahan_gcells": upd / ms16_k2 / 1e6,
                            "speedup_bf16_vs_f32": ms32_k2 / ms16_k2},
             "heat_sum_fp64": {"ms": ms_sum, "gbs": N * 4 / ms_sum / 1e6, "frac_hbm": N * 4 / ms_sum / 1e6 / hbm},
-            "note": "error vs the FP64 oracle is measured in tests/test_gpu_precision.py"}
+            "note": "errors vs the FP64 oracle at this size (2000 steps, FP32 and both BF16 forms, also "
+                    "against FP64 on the bf16-quantised inputs) are measured by "
+                    "tests/test_gpu_precision.py::test_precision_workload_full_size_against_fp64"}
 
 
 def form_batched(L, cpb, dev, stream, ngrids=4096):
@@ -362,6 +377,22 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     ms_b = ms_total - ms_copy
     status = L.cpb_batch_status(work, stream=sh)
     upd = bt.updates
+    # The workload as stated: the one persistent launch captured in a CUDA
+    # graph and replayed.  Replays run back to back on the buffers the
+    # previous replay left (the work does not depend on the values).
+    uin.copy_(u)
+    torch.cuda.synchronize()
+    cap = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        L.cpb_stencil_batched(d_descs, d_order, bt.ngrids, n_large, cpb.CPB_F32, W.DIRICHLET, plan, work,
+                              stream=cap)
+    ms_graph = _time(graph.replay, 3, stream)
+    status_graph = L.cpb_batch_status(work, stream=sh)
+    del graph
+    hbm, hsrc = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = batch_roofline(bt, plan["depth"], ms_graph, sms, hbm, hsrc)
     # one-grid-at-a-time baseline (tuned single-grid path, one call per grid)
     scratch = torch.empty(int(cells.max()), dtype=torch.float32, device=dev)
 
@@ -378,13 +409,51 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     return {"workload": f"batch-{bt.ngrids}-grids-32..1024-steps-10..500", "updates": upd,
             "cells": int(cells.sum()), "n_large": n_large, "plan": plan,
             "grain_sweep_ms": {f"depth{d}_grain{g}_threads{t}": v for (d, g, t), v in sweep.items()},
-            "batched": {"gcells": upd / ms_b / 1e6, "ms": ms_b, "status": status},
+            "batched": {"gcells": upd / ms_b / 1e6, "ms": ms_b, "status": status,
+                        "timing": "bare launch, u_in restored before each (copy time subtracted)"},
+            "batched_cuda_graph": {"gcells": upd / ms_graph / 1e6, "ms": ms_graph, "status": status_graph,
+                                   "timing": "the persistent launch captured once in a CUDA graph, "
+                                             "replayed back to back"},
+            "roofline": roof,
             "one_grid_at_a_time": {"gcells": upd / ms_each / 1e6, "ms": ms_each,
                                    "launches": n_launch_each,
                                    "note": "one cpb_stencil_launch_tuned call per grid from Python at "
                                            "the default depth 4, i.e. launch-bound: the cost the "
                                            "single persistent launch removes"},
-            "speedup_batched_vs_per_grid": ms_each / ms_b}
+            "speedup_batched_vs_per_grid": ms_each / ms_graph}
+
+
+def batch_roofline(bt, depth, ms, sms, hbm, peak_source="measured", onchip_cells=14336):
+    """Lower bound on the batched launch, per class of grid (max of the HBM
+    and the FP32-lane time of each class, summed over classes).  Grids whose
+    u, kappa, s and ping-pong partner fit in one SM's 227 KB of shared memory
+    (16 B per cell: at most 14336 cells) could run all their steps on chip:
+    their fields cross HBM once per run.  Every other grid streams its fields
+    once per pass of the plan's depth.  FP32 lanes: 10 operations per
+    cell-update (flux form) on all SMs at the maximum SM clock."""
+    src = peak_source
+    lane_rate = sms * 128 * 2070e6 / 10.0           # cell-updates per second
+    cells = bt.nx.astype(np.int64) * bt.ny.astype(np.int64)
+    steps = bt.steps.astype(np.int64)
+    small = cells <= onchip_cells
+    passes = -(-steps // depth)
+    bytes_small = float(16 * cells[small].sum())
+    bytes_large = float(16 * (cells[~small] * passes[~small]).sum())
+    upd_small = float((cells[small] * steps[small]).sum())
+    upd_large = float((cells[~small] * steps[~small]).sum())
+    t_small = max(bytes_small / (hbm * 1e9), upd_small / lane_rate)
+    t_large = max(bytes_large / (hbm * 1e9), upd_large / lane_rate)
+    bound_ms = (t_small + t_large) * 1e3
+    return {"bound": "hbm" if bytes_large / (hbm * 1e9) >= upd_large / lane_rate else "alu",
+            "time_bound_ms": bound_ms, "measured_ms": ms, "frac": bound_ms / ms,
+            "classes": {"on_chip": {"grids": int(small.sum()), "hbm_bytes": bytes_small, "updates": upd_small,
+                                    "t_hbm_ms": bytes_small / (hbm * 1e9) * 1e3,
+                                    "t_fp32_lanes_ms": upd_small / lane_rate * 1e3},
+                        "streamed": {"grids": int((~small).sum()), "hbm_bytes": bytes_large,
+                                     "updates": upd_large, "t_hbm_ms": bytes_large / (hbm * 1e9) * 1e3,
+                                     "t_fp32_lanes_ms": upd_large / lane_rate * 1e3}},
+            "peak": f"{hbm} GB/s ({src}); FP32 lanes {sms} SMs x 128 at 2070 MHz, 10 operations per update",
+            "depth": depth}
 
 
 def form_adjoint(L, cpb, dev, stream):
@@ -412,12 +481,16 @@ def form_adjoint(L, cpb, dev, stream):
 
     ms_grad = _time(grad, 3, stream)
     upd = nx * ny * T
+    ndir = 64
     return {"workload": g.name, "forward": {"gcells": upd / ms_fwd / 1e6, "ms": ms_fwd},
             "gradient": {"ms": ms_grad, "gcells_equiv": upd / ms_grad / 1e6,
                          "ratio_to_forward": ms_grad / ms_fwd},
             "fd_cost_per_direction_ms": 2 * ms_fwd,
-            "note": "one gradient = forward with checkpoints + recompute + adjoint sweep; "
-                    "central FD needs 2 forwards per direction"}
+            "fd_64_directions_ms": 2 * ndir * ms_fwd,
+            "speedup_gradient_vs_fd_64_directions": 2 * ndir * ms_fwd / ms_grad,
+            "note": "one gradient (both dL/du0 and dL/dkappa in full) = forward with checkpoints + recompute + "
+                    "adjoint sweep; central differences need 2 forwards per direction, and the workload checks "
+                    "64 directions (each for u0 and kappa)"}
 
 
 def form_volume(L, cpb, dev, stream, n=512, steps=100):

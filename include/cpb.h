@@ -436,6 +436,54 @@ cpb_status cpb_graph_create(void* u_in, void* u_out, const void* kappa, const vo
 cpb_status cpb_graph_launch(cpb_graph_t graph, cpb_stream_t stream);
 cpb_status cpb_graph_destroy(cpb_graph_t graph);
 
+/* Slab decomposition across ranks (one rank per GPU).  The paper has no
+ * multi-device runtime; this is the decomposition the stencil takes when it
+ * is spread over several GPUs, each running the single-GPU path on its slab.
+ * Rank r of `world` owns the contiguous rows [row_lo, row_hi) of the
+ * ny x nx grid (full width; sizes differ by at most one row) and keeps
+ * `depth` halo rows on each side that has a neighbouring rank (both sides
+ * for a periodic grid, a ring; none past a Dirichlet edge, where the slab's
+ * edge is the grid's).  A slab buffer holds halo_lo + (row_hi - row_lo) +
+ * halo_hi rows of nx cells, own rows starting at row halo_lo.  One round:
+ * cpb_slab_exchange fills the halos from the neighbours' own rows, then
+ * cpb_slab_step advances up to `depth` steps; the error of the cut edges
+ * moves inward one row per step, so the own rows are exact after it.
+ *
+ * cpb_slab_rows: host only.  world >= 1, 0 <= rank < world, depth >= 1,
+ * every rank must own at least `depth` rows (ny >= world * depth), else
+ * CPB_ERR_INVALID_VALUE.  Any output pointer may be NULL. */
+cpb_status cpb_slab_rows(int ny, int world, int rank, int depth, cpb_boundary bc, int* row_lo, int* row_hi,
+                         int* halo_lo, int* halo_hi);
+
+/* Fill this slab's halo rows: rows [0, halo_lo) from the lower neighbour's
+ * last halo_lo own rows, rows [halo_lo + n_own, + halo_hi) from the upper
+ * neighbour's first halo_hi own rows.  `below` / `above`: the neighbours'
+ * slab buffers (own rows starting at their row below_halo_lo / above_halo_lo;
+ * the lower neighbour owns below_n_own rows), device memory of this or a
+ * peer device (one cudaMemcpyAsync per side, cudaMemcpyDefault, on
+ * `stream`: device to device, or peer to peer through unified addressing).
+ * A side with halo 0 is skipped and its pointer may be NULL.  With one rank
+ * and a periodic grid, below and above are the slab itself.  Element size
+ * from dtype (4 bytes for every storage format).  The caller orders the
+ * exchange after the neighbours' last step (stream order or events).
+ * Validation: nx, n_own >= 1, halos in [0, n_own] and not above the
+ * neighbours' own row counts, non-null buffers for non-empty sides; else
+ * CPB_ERR_INVALID_VALUE.  Not measured on a machine with more than one GPU. */
+cpb_status cpb_slab_exchange(void* slab, int nx, int n_own, int halo_lo, int halo_hi, const void* below,
+                             int below_halo_lo, int below_n_own, const void* above, int above_halo_lo,
+                             int above_n_own, cpb_dtype dtype, cpb_stream_t stream);
+
+/* One pass of `steps` (1 <= steps <= min of the non-zero halos, and <= 8)
+ * steps over the whole slab buffer (rows_total = halo_lo + n_own + halo_hi)
+ * under the grid's boundary rule, u_in -> u_out (u_in untouched), kappa and
+ * src slab buffers of the same shape whose halos hold the neighbours' rows
+ * (they never change: exchange them once).  The tuned streaming path with
+ * depth = steps, one launch; tuning NULL: the cached / default tuning of the
+ * slab's shape.  Only the own rows of u_out are valid afterwards. */
+cpb_status cpb_slab_step(const void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                         int rows_total, int halo_lo, int halo_hi, int steps, float dt, cpb_boundary bc,
+                         cpb_dtype dtype, const cpb_tuning* tuning, cpb_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -123,6 +123,9 @@ _SIGS = {
                                  _vp]),
     "cpb_graph_create": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, C.POINTER(cpb_tuning),
                               _vp, C.POINTER(_vp)]),
+    "cpb_slab_rows": (_i, [_i, _i, _i, _i, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
+    "cpb_slab_exchange": (_i, [_vp, _i, _i, _i, _i, _vp, _i, _i, _vp, _i, _i, _i, _vp]),
+    "cpb_slab_step": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _i, _i, C.POINTER(cpb_tuning), _vp]),
     "cpb_graph_launch": (_i, [_vp, _vp]),
     "cpb_graph_destroy": (_i, [_vp]),
 }
@@ -368,6 +371,23 @@ class Library:
         self._call("cpb_graph_create", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, ny, steps,
                    float(dt), bc, dtype, t, ptr(scratch), C.byref(g))
         return g.value
+
+    def cpb_slab_rows(self, ny, world, rank, depth, bc) -> dict:
+        lo, hi, hl, hh = _i(), _i(), _i(), _i()
+        self._call("cpb_slab_rows", ny, world, rank, depth, bc, C.byref(lo), C.byref(hi), C.byref(hl),
+                   C.byref(hh))
+        return {"row_lo": lo.value, "row_hi": hi.value, "halo_lo": hl.value, "halo_hi": hh.value}
+
+    def cpb_slab_exchange(self, slab, nx, n_own, halo_lo, halo_hi, below, below_halo_lo, below_n_own, above,
+                          above_halo_lo, above_n_own, dtype, stream=None):
+        self._call("cpb_slab_exchange", ptr(slab), nx, n_own, halo_lo, halo_hi, ptr(below), below_halo_lo,
+                   below_n_own, ptr(above), above_halo_lo, above_n_own, dtype, stream_handle(stream))
+
+    def cpb_slab_step(self, u_in, u_out, kappa, src, nx, rows_total, halo_lo, halo_hi, steps, dt, bc, dtype,
+                      tuning=None, stream=None):
+        t = C.byref(as_tuning(tuning)) if tuning is not None else None
+        self._call("cpb_slab_step", ptr(u_in), ptr(u_out), ptr(kappa), ptr(src), nx, rows_total, halo_lo,
+                   halo_hi, steps, float(dt), bc, dtype, t, stream_handle(stream))
 
     def cpb_graph_launch(self, graph, stream=None):
         self._call("cpb_graph_launch", graph, stream_handle(stream))

@@ -1028,6 +1028,64 @@ cpb_status cpb_stencil_adjoint(const float* u0, const float* kappa, const float*
                               grad_kappa, workspace, ws_bytes, stream);
 }
 
+// ---------------------------------------------------------------------------
+// Slab decomposition (one rank per GPU)
+// ---------------------------------------------------------------------------
+cpb_status cpb_slab_rows(int ny, int world, int rank, int depth, cpb_boundary bc, int* row_lo, int* row_hi,
+                         int* halo_lo, int* halo_hi) {
+  if (world < 1 || rank < 0 || rank >= world || depth < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  if (bc != CPB_DIRICHLET0 && bc != CPB_PERIODIC) return CPB_ERR_INVALID_VALUE;
+  if ((long long)world * depth > ny) return CPB_ERR_INVALID_VALUE;
+  const int base = ny / world, extra = ny % world;
+  const int lo = rank * base + std::min(rank, extra);
+  const int hi = lo + base + (rank < extra ? 1 : 0);
+  const bool periodic = bc == CPB_PERIODIC;
+  if (row_lo) *row_lo = lo;
+  if (row_hi) *row_hi = hi;
+  if (halo_lo) *halo_lo = (periodic || rank > 0) ? depth : 0;
+  if (halo_hi) *halo_hi = (periodic || rank < world - 1) ? depth : 0;
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_slab_exchange(void* slab, int nx, int n_own, int halo_lo, int halo_hi, const void* below,
+                             int below_halo_lo, int below_n_own, const void* above, int above_halo_lo,
+                             int above_n_own, cpb_dtype dtype, cpb_stream_t stream) {
+  if (!slab || nx < 1 || n_own < 1 || !dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
+  if (halo_lo < 0 || halo_hi < 0 || halo_lo > n_own || halo_hi > n_own) return CPB_ERR_INVALID_VALUE;
+  if (halo_lo > 0 && (!below || below_halo_lo < 0 || below_n_own < halo_lo)) return CPB_ERR_INVALID_VALUE;
+  if (halo_hi > 0 && (!above || above_halo_lo < 0 || above_n_own < halo_hi)) return CPB_ERR_INVALID_VALUE;
+  const size_t row = (size_t)nx * u_bytes(dtype);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* dst = static_cast<char*>(slab);
+  if (halo_lo > 0) {
+    const char* src = static_cast<const char*>(below) + (size_t)(below_halo_lo + below_n_own - halo_lo) * row;
+    CPB_TRY(cudaMemcpyAsync(dst, src, (size_t)halo_lo * row, cudaMemcpyDefault, s));
+  }
+  if (halo_hi > 0) {
+    const char* src = static_cast<const char*>(above) + (size_t)above_halo_lo * row;
+    CPB_TRY(cudaMemcpyAsync(dst + (size_t)(halo_lo + n_own) * row, src, (size_t)halo_hi * row,
+                            cudaMemcpyDefault, s));
+  }
+  return CPB_SUCCESS;
+}
+
+cpb_status cpb_slab_step(const void* u_in, void* u_out, const void* kappa, const void* src, int nx,
+                         int rows_total, int halo_lo, int halo_hi, int steps, float dt, cpb_boundary bc,
+                         cpb_dtype dtype, const cpb_tuning* tuning, cpb_stream_t stream) {
+  if (halo_lo < 0 || halo_hi < 0 || (long long)halo_lo + halo_hi >= rows_total) return CPB_ERR_INVALID_VALUE;
+  if (steps < 1 || steps > 8 || (halo_lo > 0 && steps > halo_lo) || (halo_hi > 0 && steps > halo_hi))
+    return CPB_ERR_INVALID_VALUE;
+  // One pass (steps <= the tuning's depth): it reads u_in and writes u_out,
+  // so u_in is left as it was.
+  Fields f{const_cast<void*>(u_in), u_out, kappa, src, nullptr};
+  cpb_status st = check_common(f, nx, rows_total, steps, dt, bc, dtype);
+  if (st != CPB_SUCCESS) return st;
+  cpb_tuning t = tuning ? *tuning : lookup_tuning(nx, rows_total, dtype, bc);
+  if (t.k < steps) t.k = steps;
+  if (!tuning_valid(t)) return CPB_ERR_UNSUPPORTED_CONFIG;
+  return enqueue_tuned(f, nx, rows_total, steps, dt, bc, dtype, t, reinterpret_cast<cudaStream_t>(stream));
+}
+
 cpb_status cpb_graph_create(void* u_in, void* u_out, const void* kappa, const void* src, int nx,
                             int ny, int steps, float dt, cpb_boundary bc, cpb_dtype dtype,
                             const cpb_tuning* tuning, void* scratch, cpb_graph_t* graph) {

@@ -109,3 +109,46 @@ def test_batch_order_is_host_only_lpt(L):
     assert status(L.cpb_batch_order, descs, None) == INV
     assert status(L.cpb_batch_order, descs, {"grain": 0}) == INV
     assert status(L.cpb_batch_order, descs, {"grain": 1, "depth": 8, "threads": 384}) == INV
+
+
+def test_slab_rows_match_the_row_split(L):
+    # The library's split rule against the slab decomposition of the oracle's
+    # CPU ranks (sizes differ by at most one, in rank order) and the halo rule.
+    from oracle.slab import split_rows
+    for ny in (8, 15, 61, 100, 1000):
+        for world in (1, 2, 3, 5):
+            for depth in (1, 2, 3):
+                if world * depth > ny:
+                    assert status(L.cpb_slab_rows, ny, world, 0, depth, D) == INV
+                    continue
+                parts = split_rows(ny, world)
+                for rank in range(world):
+                    for bc in (D, P):
+                        r = L.cpb_slab_rows(ny, world, rank, depth, bc)
+                        assert (r["row_lo"], r["row_hi"]) == parts[rank]
+                        assert r["halo_lo"] == (depth if (bc == P or rank > 0) else 0)
+                        assert r["halo_hi"] == (depth if (bc == P or rank < world - 1) else 0)
+    assert status(L.cpb_slab_rows, 10, 2, 2, 1, D) == INV
+    assert status(L.cpb_slab_rows, 10, 2, 0, 0, D) == INV
+    assert status(L.cpb_slab_rows, 10, 2, 0, 1, 7) == INV
+
+
+def test_slab_exchange_and_step_validation(L):
+    assert status(L.cpb_slab_exchange, None, 64, 10, 2, 2, U, 2, 10, U, 2, 10, F32, stream=0) == INV
+    assert status(L.cpb_slab_exchange, X, 64, 10, 2, 2, None, 2, 10, U, 2, 10, F32, stream=0) == INV
+    assert status(L.cpb_slab_exchange, X, 64, 10, 2, 2, U, 2, 1, U, 2, 10, F32, stream=0) == INV  # neighbour too small
+    assert status(L.cpb_slab_exchange, X, 64, 10, 11, 0, U, 2, 20, None, 0, 0, F32, stream=0) == INV
+    assert status(L.cpb_slab_exchange, X, 64, 10, 2, 2, U, 2, 10, U, 2, 10, 9, stream=0) == INV
+    assert status(L.cpb_slab_step, U, O, K, S, 64, 14, 2, 2, 3, 0.1, D, F32, stream=0) == INV      # steps > halo
+    assert status(L.cpb_slab_step, U, O, K, S, 64, 14, 2, 2, 0, 0.1, D, F32, stream=0) == INV
+    assert status(L.cpb_slab_step, U, O, K, S, 64, 4, 2, 2, 1, 0.1, D, F32, stream=0) == INV       # no own rows
+    assert status(L.cpb_slab_step, U, U, K, S, 64, 14, 2, 2, 2, 0.1, D, F32, stream=0) == INV      # in place
+
+
+def test_bf16_block_dtype_is_accepted_and_validated(L):
+    BB = cpb.CPB_BF16_KAHAN_BLOCK
+    assert status(L.cpb_stencil_launch_tuned, U, U, K, S, 64, 32, 4, 0.1, D, BB, stream=0) == INV   # in place
+    assert status(L.cpb_stencil_launch_tuned, U, O, K, S, 64, 32, 4, 0.1, D, 3, stream=0) == INV    # unknown dtype
+    assert status(L.cpb_stencil_launch, U, O, K, S, 64, 32, 4, 0.1, D, BB, (4, 2, 1), (16, 16, 1),
+                  2 * 18 * 18 * 4, stream=0) == UNS                                            # tiled kernel: FP32 only
+    assert L.cpb_host_workspace_bytes(64, 64, BB) == L.cpb_host_workspace_bytes(64, 64, BF)

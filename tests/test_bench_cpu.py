@@ -29,3 +29,20 @@ def test_warmup_is_at_least_three():
                        timeout=600)
     assert r.returncode == 0, r.stderr
     assert json.loads(r.stdout.strip().splitlines()[-1])["warmup"] == 3
+
+
+def test_batch_roofline_per_class_bound():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    bt = W.batching(ngrids=64)
+    r = bench.batch_roofline(bt, 4, 10.0, sms=152, hbm=6000.0)
+    cls = r["classes"]
+    assert cls["on_chip"]["grids"] + cls["streamed"]["grids"] == 64
+    assert abs(cls["on_chip"]["updates"] + cls["streamed"]["updates"] - bt.updates) < 1
+    want = (max(cls["on_chip"]["t_hbm_ms"], cls["on_chip"]["t_fp32_lanes_ms"])
+            + max(cls["streamed"]["t_hbm_ms"], cls["streamed"]["t_fp32_lanes_ms"]))
+    assert abs(r["time_bound_ms"] - want) < 1e-9 and abs(r["frac"] - want / 10.0) < 1e-12
+    # a deeper plan streams fewer bytes for the same updates
+    assert bench.batch_roofline(bt, 8, 10.0, sms=152, hbm=6000.0)["classes"]["streamed"]["hbm_bytes"] < \
+        cls["streamed"]["hbm_bytes"]

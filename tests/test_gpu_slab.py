@@ -1,14 +1,16 @@
-"""The slab decomposition on one GPU with the library's own kernels.
+"""The slab decomposition on one GPU through the library's slab calls.
 
 Ranks are emulated in one process, one after another, with no kernel waiting
-on another.  Rank r's slab lives in its own device buffer: its own rows plus
-K halo rows on each side that has a neighbour.  Every K steps the halos are
-filled by device-to-device copies of the neighbours' own rows (a ring for
-periodic boundaries).  Then one depth-K pass of the stream kernel runs on
-each slab under the grid's own boundary rule.  The rows at a slab's cut
-edges see a wrong boundary, but the error moves inward by one row per step,
-so after K steps the own rows are exact.  A slab at a Dirichlet edge has no
-halo on that side: its buffer edge is the true boundary.
+on another.  cpb_slab_rows gives rank r its own rows and halo sizes; rank r's
+slab lives in its own device buffers (u, kappa, s): its own rows plus K halo
+rows on each side that has a neighbour.  kappa and s halos are exchanged once
+(they never change); every K steps cpb_slab_exchange fills the u halos from
+the neighbours' own rows (a ring for periodic boundaries), then cpb_slab_step
+runs one pass of up to K steps on each slab under the grid's own boundary
+rule.  The rows at a slab's cut edges see a wrong boundary, but the error
+moves inward by one row per step, so after the pass the own rows are exact.
+A slab at a Dirichlet edge has no halo on that side: its buffer edge is the
+true boundary.
 
 The assembled result of the --fmad=false build must equal the FP32 oracle bit
 for bit, and the whole-grid run of the same library.
@@ -18,7 +20,6 @@ import pytest
 
 import oracle
 import workloads as W
-from oracle.slab import split_rows
 
 torch = pytest.importorskip("torch")
 cpb = pytest.importorskip("paper_2206_07896_gb300")
@@ -34,49 +35,44 @@ def dev():
     return torch.device("cuda:0")
 
 
-def run_slabs(L, g, world, K, dev, tuning_extra):
+def run_slabs(L, g, world, K, dev, tuning):
     ny, nx = g.u.shape
-    periodic = g.bc == P
-    parts = split_rows(ny, world)
-    # halo rows below / above each rank's own rows (none past a Dirichlet edge)
-    lo_h = [K if (periodic or r > 0) else 0 for r in range(world)]
-    hi_h = [K if (periodic or r < world - 1) else 0 for r in range(world)]
+    F = cpb.CPB_F32
+    lay = [L.cpb_slab_rows(ny, world, r, K, g.bc) for r in range(world)]
+    n = [x["row_hi"] - x["row_lo"] for x in lay]
+    hl = [x["halo_lo"] for x in lay]
+    hh = [x["halo_hi"] for x in lay]
+    rows = [hl[r] + n[r] + hh[r] for r in range(world)]
 
-    def rows(r):  # global row of every local row of rank r (wrapped)
-        lo, hi = parts[r]
-        return np.arange(lo - lo_h[r], hi + hi_h[r]) % ny
+    def slab_of(field):  # own rows placed, halos zero (filled by the exchange)
+        out = []
+        for r in range(world):
+            t = torch.zeros((rows[r], nx), dtype=torch.float32, device=dev)
+            t[hl[r]:hl[r] + n[r]] = torch.from_numpy(field[lay[r]["row_lo"]:lay[r]["row_hi"]]).to(dev)
+            out.append(t)
+        return out
 
-    u, kap, src, out = [], [], [], []
-    for r in range(world):
-        idx = rows(r)
-        u.append(torch.from_numpy(np.ascontiguousarray(g.u[idx])).to(dev))
-        kap.append(torch.from_numpy(np.ascontiguousarray(g.kappa[idx])).to(dev))  # static halos, once
-        src.append(torch.from_numpy(np.ascontiguousarray(g.src[idx])).to(dev))
-        out.append(torch.empty_like(u[-1]))
-    n = [hi - lo for lo, hi in parts]
+    def exchange(bufs):
+        for r in range(world):
+            b, a = (r - 1) % world, (r + 1) % world
+            L.cpb_slab_exchange(bufs[r], nx, n[r], hl[r], hh[r], bufs[b] if hl[r] else None, hl[b], n[b],
+                                bufs[a] if hh[r] else None, hl[a], n[a], F)
 
-    def own(r, t):
-        return t[r][lo_h[r]:lo_h[r] + n[r]]
-
+    u, kap, src = slab_of(g.u), slab_of(g.kappa), slab_of(g.src)
+    exchange(kap)        # static fields: halos once
+    exchange(src)
+    out = [torch.empty_like(x) for x in u]
     done = 0
     while done < g.steps:
         k = min(K, g.steps - done)
-        for r in range(world):  # halo exchange: neighbours' own rows into this slab's halos
-            if lo_h[r]:
-                below = (r - 1) % world
-                u[r][:K].copy_(own(below, u)[n[below] - K:])
-            if hi_h[r]:
-                above = (r + 1) % world
-                u[r][lo_h[r] + n[r]:].copy_(own(above, u)[:K])
+        exchange(u)
         for r in range(world):
-            t = {"k": K, **tuning_extra}
-            L.cpb_stencil_launch_tuned(u[r], out[r], kap[r], src[r], nx, u[r].shape[0], k, float(g.dt), g.bc,
-                                       cpb.CPB_F32, tuning=t)
-        for r in range(world):
-            own(r, u).copy_(own(r, out))
+            L.cpb_slab_step(u[r], out[r], kap[r], src[r], nx, rows[r], hl[r], hh[r], k, float(g.dt), g.bc, F,
+                            tuning=tuning)
+        u, out = out, u
         done += k
     torch.cuda.synchronize()
-    return np.concatenate([own(r, u).cpu().numpy() for r in range(world)], axis=0)
+    return np.concatenate([u[r][hl[r]:hl[r] + n[r]].cpu().numpy() for r in range(world)], axis=0)
 
 
 @pytest.mark.parametrize("bc", [P, D])
@@ -85,12 +81,13 @@ def run_slabs(L, g, world, K, dev, tuning_extra):
     (3, 8, 384, 100, 17),   # depth 8 (rows in pairs)
     (4, 2, 203, 61, 7),     # register-prefetch rows (nx % 4 != 0), ragged split
     (5, 3, 256, 15, 9),     # ranks owning exactly K rows
+    (1, 4, 256, 40, 10),    # one rank: a periodic slab's halos are its own wrapped rows
 ])
 def test_slabs_equal_oracle_and_whole_grid(dev, bc, world, K, nx, ny, steps):
     L = cpb.lib(fma=False)
     g = W.random_grid(40 + world, nx, ny, steps, bc)
     variant = 1 if nx % 4 == 0 else 0
-    res = run_slabs(L, g, world, K, dev, {"chunk_rows": 64, "warps_per_block": 2, "variant": variant,
+    res = run_slabs(L, g, world, K, dev, {"k": K, "chunk_rows": 64, "warps_per_block": 2, "variant": variant,
                                            "stages": 4})
     ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, g.bc, "f32")
     assert np.array_equal(res, ref)
