@@ -844,21 +844,24 @@ __device__ __forceinline__ bool item_interior(const StreamArgs& a, int item) {
          y1 + a.depth <= a.ny;
 }
 
-// EDGES (single-grid kernels): the items of a Dirichlet grid that touch no
-// edge run the periodic body (unrolled, no masks); the edge items run the
-// masked body with its row loop not unrolled, so that one large loop body is
-// live on a multiprocessor (two unrolled bodies executing side by side cost
-// more in instruction fetch than the masks they save: measured at 8192^2,
-// depth 8, 505 -> 652 us per pass).  Without EDGES (the batched kernel, whose
-// small grids are mostly edge items) every Dirichlet item takes the masked
-// unrolled body.
+// EDGES (single-grid kernels, depth <= 6): the items of a Dirichlet grid
+// that touch no edge run the periodic body (unrolled, no masks); the edge
+// items run the masked body with its row loop not unrolled, so that one large
+// loop body is live on a multiprocessor (two unrolled bodies executing side
+// by side cost more in instruction fetch than the masks they save: measured
+// at 8192^2, depth 8, 505 -> 652 us per pass).  Measured per pass on GB300:
+// 16384^2 Dirichlet depth 4 915 -> 865 us, depth 6 1708 -> 1515 us.  At depth
+// 8 the changed register allocation slowed the periodic body itself (8192^2:
+// 385 -> 433 us), so depth 8, and the batched kernel (whose small grids are
+// mostly edge items), keep the masked unrolled body for every Dirichlet item.
 template <int K, bool BF, bool FULL, bool LV = false, bool RE = true, bool EDGES = false>
 __device__ __forceinline__ bool bulk_item(const StreamArgs& a, int item, int lane, unsigned char* ring,
                                           uint64_t* bars, float4* face, int* status,
                                           const LevelOut* lv = nullptr) {
-  if (a.bc == BC_PERIODIC || (EDGES && item_interior<K, BF>(a, item)))
+  constexpr bool SPLIT = EDGES && K <= 6;
+  if (a.bc == BC_PERIODIC || (SPLIT && item_interior<K, BF>(a, item)))
     return bulk_item_bc<K, BF, FULL, true, LV, RE>(a, item, lane, ring, bars, face, status, lv);
-  return bulk_item_bc<K, BF, FULL, false, LV, RE, !EDGES>(a, item, lane, ring, bars, face, status, lv);
+  return bulk_item_bc<K, BF, FULL, false, LV, RE, !SPLIT>(a, item, lane, ring, bars, face, status, lv);
 }
 
 // Shared memory of a CTA of `nwarps` warps using the row ring:
