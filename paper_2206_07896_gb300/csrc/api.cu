@@ -961,7 +961,15 @@ cpb_status cpb_adjoint_backward(const float* kappa, const float* src, const floa
                                     src);
   StreamPass lp;
   if (levels) {
-    const cpb_tuning t4 = default_tuning(nx, ny, CPB_F32);  // depth 4, TMA ring
+    // depth 4 and the TMA ring (the level-storing kernel's); chunk height,
+    // CTA size and ring depth from the grid's tuning when it uses the ring
+    cpb_tuning t4 = default_tuning(nx, ny, CPB_F32);
+    const cpb_tuning tc = lookup_tuning(nx, ny, CPB_F32, bc);
+    if (tc.variant == 1) {
+      t4.chunk_rows = tc.chunk_rows;
+      t4.warps_per_block = tc.warps_per_block;
+      t4.stages = tc.stages;
+    }
     lp.kappa = kappa;
     lp.src = src;
     lp.nx = nx;
@@ -979,6 +987,10 @@ cpb_status cpb_adjoint_backward(const float* kappa, const float* src, const floa
     lp.inject_row = 0;
     lp.store_levels = 1;
   }
+  // Temporally blocked adjoint passes need the 16-byte row path of every
+  // field they touch (workspace slots are 256-byte aligned).
+  const bool blocked = nx % 4 == 0 && aligned(lambda_T, 16) && aligned(kappa, 16) && aligned(grad_kappa, 16) &&
+                       aligned(grad_u0, 16);
   const float* lam_cur = lambda_T;
   int flip = 0;
   for (int m = L.nseg - 1; m >= 0; --m) {
@@ -1003,12 +1015,23 @@ cpb_status cpb_adjoint_backward(const float* kappa, const float* src, const floa
         if (st != CPB_SUCCESS) return st;
       }
     }
-    for (int q = len - 1; q >= 0; --q) {
-      const float* un = q == 0 ? L.ckpt(workspace, m) : L.seg(workspace, q - 1);
-      float* out = (m == 0 && q == 0) ? grad_u0 : L.lam(workspace, flip);
-      CPB_TRY(launch_adjoint_step(lam_cur, out, un, kappa, grad_kappa, nx, ny, dt, (int)bc, s));
+    // Backward sweep of the segment: lambda_{a+q+1} -> lambda_{a+q} for q =
+    // len-1 .. 0 uses state u_{a+q}.  Where the 16-byte row path applies, in
+    // passes of up to 4 steps (the same bits as one launch per step).
+    auto state = [&](int q) -> const float* { return q == 0 ? L.ckpt(workspace, m) : L.seg(workspace, q - 1); };
+    for (int q = len - 1; q >= 0;) {
+      const int d = blocked ? std::min(4, q + 1) : 1;  // steps q, q-1, .. q-d+1
+      float* out = (m == 0 && q - d + 1 == 0) ? grad_u0 : L.lam(workspace, flip);
+      if (blocked) {
+        const float* us[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int t = 1; t <= d; ++t) us[t - 1] = state(q - t + 1);
+        CPB_TRY(launch_adjoint_pass(lam_cur, out, us, d, kappa, grad_kappa, nx, ny, dt, (int)bc, 0, s));
+      } else {
+        CPB_TRY(launch_adjoint_step(lam_cur, out, state(q), kappa, grad_kappa, nx, ny, dt, (int)bc, s));
+      }
       lam_cur = out;
       flip ^= 1;
+      q -= d;
     }
   }
   return CPB_SUCCESS;

@@ -90,4 +90,24 @@ __device__ __forceinline__ uint32_t kahan_round(float v, float& eff) {
   return hi | (cm << 16);
 }
 
+// Per-thread asynchronous copies global -> shared (cp.async): 16 or 4 bytes,
+// src_bytes = 0 fills the destination with zeros (the source address must
+// still be a valid one).  One commit group per call of cp_async_commit;
+// cp_async_wait<N> returns once at most N of this thread's groups are pending.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 }  // namespace cpb

@@ -108,6 +108,11 @@ namespace cpb {
 // One adjoint step (k_adjoint.cu): lam_out = lam + dt D lam; gk += face terms.
 cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u, const float* k,
                                 float* gk, int nx, int ny, float dt, int bc, cudaStream_t s);
+// `depth` adjoint steps in one pass (k_adjoint.cu), lam = lambda_m ->
+// lam_out = lambda_{m-depth}; u[t - 1] = u_{m-t}.  nx % 4 == 0, 16-byte
+// aligned fields, depth 1..4; the same bits as `depth` one-step launches.
+cudaError_t launch_adjoint_pass(const float* lam, float* lam_out, const float* const* u, int depth, const float* k,
+                                float* gk, int nx, int ny, float dt, int bc, int chunk_rows, cudaStream_t s);
 }  // namespace cpb
 
 namespace cpb {

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "k_stream.cuh"
 
 namespace cpb {
 namespace {
@@ -220,7 +221,254 @@ cudaError_t resident_warps(int* out) {
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Temporally blocked adjoint: D steps per pass
+// ---------------------------------------------------------------------------
+// One pass advances lambda D steps backwards, lambda_{m} -> lambda_{m-D}, and
+// adds the D steps' kappa-gradient terms, so lambda, kappa and the gradient
+// cross memory once per D steps instead of once per step (each level still
+// reads its own forward state u_{m-t}).  The lambda recursion is the forward
+// update with no source, so it runs on the streaming kernel's register
+// pipeline (Pipe, flux form): a warp owns a 128-column strip and a chunk of
+// rows, level t makes row rho = r_in - t of lambda_{m-t} from level t-1's rows.
+// Next to it, level t forms the gradient terms of the same row from the
+// level's input rows (lambda_{m-t+1}) and the rows rho, rho + 1 of u_{m-t}:
+// the face product hdt (u_f - u_c)(lambda_c - lambda_f) of an interior face
+// is the same number seen from either cell (both factors change sign
+// exactly), so each east and north face is formed once, the west face comes
+// from the lane to the west (shuffle) and the south face is the north face of
+// the row below at the same level, carried in registers; a Dirichlet boundary
+// face takes dt (0 - u_c) lambda_c.  A row's accumulator is loaded from the
+// gradient buffer when the row enters level 1 and receives the terms of
+// levels 1, 2, .. D in that order, the order in which the one-step kernel
+// adds them: the pass gives the one-step kernels' bits, whatever D.
+// nx % 4 == 0 and 16-byte aligned fields; D = 1..4 (instantiated).
+constexpr int ADJ_TB_WARPS = 1;
+constexpr int ADJ_STAGES = 4;  // rows in the per-lane copy ring (ADJ_STAGES - 1 ahead)
+
+struct AdjPassArgs {
+  const float* lam;
+  float* lam_out;
+  const float* k;
+  float* gk;
+  const float* u[4];  // u[t - 1]: the forward state of level t (u_{m-t})
+  int nx, ny;
+  float dt, hdt;
+  int bc, chunk_rows, n_strips, n_items;
+};
+
+__device__ __forceinline__ float4 boundary_term(float dt, float4 uc, float4 lc) {
+  return make_float4(dt * (0.0f - uc.x) * lc.x, dt * (0.0f - uc.y) * lc.y, dt * (0.0f - uc.z) * lc.z,
+                     dt * (0.0f - uc.w) * lc.w);
+}
+
+__device__ __forceinline__ float4 face_term(float hdt, float4 uf, float4 uc, float4 lc, float4 lf) {
+  return make_float4(hdt * (uf.x - uc.x) * (lc.x - lf.x), hdt * (uf.y - uc.y) * (lc.y - lf.y),
+                     hdt * (uf.z - uc.z) * (lc.z - lf.z), hdt * (uf.w - uc.w) * (lc.w - lf.w));
+}
+
+template <int D>
+__global__ void __launch_bounds__(32 * ADJ_TB_WARPS) adjoint_pass(const AdjPassArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int HALO = (D + 3) & ~3;
+  constexpr int OW = 128 - 2 * HALO;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * ADJ_TB_WARPS + wib;
+  if (item >= a.n_items) return;  // warp-uniform; no block-level barrier is used
+  float4* face = reinterpret_cast<float4*>(smem + (size_t)wib * face_ring_rows(D) * FACE_SLOT_BYTES);
+  const int nx = a.nx, ny = a.ny;
+  const bool periodic = a.bc == BC_PERIODIC;
+  const int strip = item % a.n_strips, chunk = item / a.n_strips;
+  const LaneCols lc = lane_cols(strip * OW - HALO + 4 * lane, nx, periodic);
+  const int y0 = chunk * a.chunk_rows, y1 = min(y0 + a.chunk_rows, ny);
+  const bool lane_out = lane >= HALO / 4 && lane < (HALO + OW) / 4 && lc.xs < nx;
+  // Dirichlet boundary faces of this lane's cells (west of x = 0, east of x = nx - 1)
+  const bool bW0 = !periodic && lc.xs == 0;
+  bool bE[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) bE[e] = !periodic && lc.xs + e == nx - 1;
+  const float4 z4 = f4(0.0f);
+
+  // Input rows reach shared memory through a per-lane ring of ADJ_STAGES
+  // slots filled by asynchronous 16-byte copies, ADJ_STAGES - 1 rows ahead
+  // (each lane copies and reads only its own 16 bytes of each field, so the
+  // lane's own wait orders them).  Slot of input row r: fields lambda row r,
+  // kappa row r, gradient row r - 1, and u_{m-t} row r - t + 1 for t = 1..D.
+  // Ghost rows (Dirichlet): zero-filled copies; kappa from the clamped row.
+  float4* ring = reinterpret_cast<float4*>(smem + (size_t)ADJ_TB_WARPS * face_ring_rows(D) * FACE_SLOT_BYTES) +
+                 (size_t)wib * ADJ_STAGES * (D + 3) * 32 + lane;
+  auto row_of = [&](int r, bool& in) -> size_t {
+    in = periodic || (r >= 0 && r < ny);
+    const int rr = periodic ? wrap_near(r, ny) : clamp_index(r, ny);
+    return (size_t)rr * nx + lc.xv;
+  };
+  auto issue = [&](int r, int slot) {
+    float4* d = ring + (size_t)slot * (D + 3) * 32;
+    bool in;
+    size_t g = row_of(r, in);
+    cp_async16(d, a.lam + g, (in && lc.cin4) ? 16 : 0);
+    cp_async16(d + 32, a.k + g, 16);
+    g = row_of(r - 1, in);
+    cp_async16(d + 64, a.gk + g, (in && lc.cin4) ? 16 : 0);
+#pragma unroll
+    for (int t = 1; t <= D; ++t) {
+      g = row_of(r - t + 1, in);
+      cp_async16(d + 32 * (2 + t), a.u[t - 1] + g, (in && lc.cin4) ? 16 : 0);
+    }
+  };
+
+  Pipe<D, false> pipe;
+  pipe.init(face, lane);
+  float4 Urow[D];  // level t: row rho of u_{m-t} (carried from the previous iteration)
+  float4 PN[D];    // level t: north-face terms of the previous row (its south faces)
+  float4 A[D];     // A[t]: gradient accumulator of the row at level t (1 .. D-1)
+#pragma unroll
+  for (int t = 0; t < D; ++t) Urow[t] = PN[t] = A[t] = z4;
+  const int r_first = y0 - D, r_end = y1 + D;
+#pragma unroll
+  for (int j = 0; j < ADJ_STAGES - 1; ++j) {
+    if (r_first + j < r_end) issue(r_first + j, j);
+    cp_async_commit();
+  }
+  auto body = [&](auto parity, int r_in) {
+    constexpr int P = decltype(parity)::value, Q = 1 - P;
+    const int i = r_in - r_first;
+    // refill the slot read last iteration, then wait for this row's copies
+    if (r_in + ADJ_STAGES - 1 < r_end) issue(r_in + ADJ_STAGES - 1, (i + ADJ_STAGES - 1) % ADJ_STAGES);
+    cp_async_commit();
+    cp_async_wait<ADJ_STAGES - 1>();
+    const float4* sl = ring + (size_t)(i % ADJ_STAGES) * (D + 3) * 32;
+    const float4 ln = sl[0], g_init = sl[64];
+    float4 kn = sl[32];
+    if (!periodic) {  // Dirichlet ghost lanes take kappa of the edge cell
+      if (lc.kb == 1) kn = f4(kn.x);
+      if (lc.kb == 2) kn = f4(kn.w);
+    }
+    float4 un[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) un[t] = sl[32 * (3 + t)];
+    float4 out;
+    uint4 packed;
+    pipe.template step<P, true>(r_in, D, ny, periodic, lc, a.dt, a.hdt, ln, kn, z4, out, packed);
+    // gradient terms of level t at row rho = r_in - t, from the level's input
+    // rows (pipe.U[t-1][Q]: row rho, pipe.U[t-1][P]: row rho + 1)
+    float4 c[D];
+#pragma unroll
+    for (int t = 1; t <= D; ++t) {
+      const int rho = r_in - t;
+      const float4 lC = pipe.U[t - 1][Q], lN = pipe.U[t - 1][P];
+      const float4 uC = Urow[t - 1], uN = un[t - 1];
+      Urow[t - 1] = uN;
+      const float uE3 = __shfl_down_sync(CPB_FULL, uC.x, 1), lE3 = __shfl_down_sync(CPB_FULL, lC.x, 1);
+      float4 pE = face_term(a.hdt, make_float4(uC.y, uC.z, uC.w, uE3), uC, lC, make_float4(lC.y, lC.z, lC.w, lE3));
+      const float4 bt = boundary_term(a.dt, uC, lC);
+      pE.x = bE[0] ? bt.x : pE.x;
+      pE.y = bE[1] ? bt.y : pE.y;
+      pE.z = bE[2] ? bt.z : pE.z;
+      pE.w = bE[3] ? bt.w : pE.w;
+      // west faces: the east terms of the cells to the west (the lane's first
+      // cell: the last of the lane to the west)
+      const float pW0 = __shfl_up_sync(CPB_FULL, pE.w, 1);
+      const float4 pW = make_float4(bW0 ? bt.x : pW0, pE.x, pE.y, pE.z);
+      float4 pN = face_term(a.hdt, uN, uC, lC, lN);
+      if (!periodic && rho + 1 >= ny) pN = bt;
+      float4 pS = PN[t - 1];
+      if (!periodic && rho - 1 < 0) pS = bt;
+      PN[t - 1] = pN;
+      c[t - 1] = make_float4((pW.x + pE.x) + (pS.x + pN.x), (pW.y + pE.y) + (pS.y + pN.y),
+                             (pW.z + pE.z) + (pS.z + pN.z), (pW.w + pE.w) + (pS.w + pN.w));
+    }
+    // accumulate: the row at level D leaves, the others move up one level
+    float4 g_out;
+    if constexpr (D == 1) {
+      g_out = make_float4(g_init.x + c[0].x, g_init.y + c[0].y, g_init.z + c[0].z, g_init.w + c[0].w);
+    } else {
+      g_out = make_float4(A[D - 2].x + c[D - 1].x, A[D - 2].y + c[D - 1].y, A[D - 2].z + c[D - 1].z,
+                          A[D - 2].w + c[D - 1].w);
+#pragma unroll
+      for (int t = D - 2; t >= 1; --t)
+        A[t] = make_float4(A[t - 1].x + c[t].x, A[t - 1].y + c[t].y, A[t - 1].z + c[t].z, A[t - 1].w + c[t].w);
+      A[0] = make_float4(g_init.x + c[0].x, g_init.y + c[0].y, g_init.z + c[0].z, g_init.w + c[0].w);
+    }
+    const int ro = r_in - D;
+    if (ro >= y0 && lane_out) {
+      const size_t g = (size_t)ro * nx + lc.xs;
+      *reinterpret_cast<float4*>(a.lam_out + g) = out;
+      *reinterpret_cast<float4*>(a.gk + g) = g_out;
+    }
+  };
+  int r_in = r_first;
+  for (; r_in + 1 < r_end; r_in += 2) {
+    body(Int<0>{}, r_in);
+    body(Int<1>{}, r_in + 1);
+  }
+  if (r_in < r_end) body(Int<0>{}, r_in);
+  cp_async_wait<0>();  // no copy may target this CTA's shared memory after it exits
+}
+
+// Shared-memory opt-in above 48 KB, once per depth and device (ordinal < 32).
+unsigned g_adj_attr_done[5];
+cudaError_t ensure_smem_optin_adj(int depth, size_t shm) {
+  const void* fn = depth == 1 ? (const void*)adjoint_pass<1>
+                   : depth == 2 ? (const void*)adjoint_pass<2>
+                   : depth == 3 ? (const void*)adjoint_pass<3>
+                                : (const void*)adjoint_pass<4>;
+  return ensure_smem_optin(fn, g_adj_attr_done[depth], shm);
+}
+
+size_t adjoint_pass_smem(int depth) {
+  return (size_t)ADJ_TB_WARPS * (face_ring_rows(depth) * FACE_SLOT_BYTES + ADJ_STAGES * (depth + 3) * 32 * 16);
+}
+
 }  // namespace
+
+cudaError_t launch_adjoint_pass(const float* lam, float* lam_out, const float* const* u, int depth, const float* k,
+                                float* gk, int nx, int ny, float dt, int bc, int chunk_rows, cudaStream_t s) {
+  if (depth < 1 || depth > 4) return cudaErrorInvalidValue;
+  if (chunk_rows < 1) {
+    // chunks sized so the items come to about one wave of resident warps
+    // (at least 16 rows: each chunk recomputes 2 x 4 halo rows)
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pass<4>, 32 * ADJ_TB_WARPS,
+                                                        adjoint_pass_smem(4));
+    if (e != cudaSuccess) return e;
+    const long long warps = std::max(1LL, (long long)sms * std::max(1, per_sm) * ADJ_TB_WARPS);
+    const long long strips = (nx + strip_out_width(4) - 1) / strip_out_width(4);
+    chunk_rows = (int)std::max(16LL, std::min((strips * ny + warps - 1) / warps, 1024LL));
+  }
+  AdjPassArgs a;
+  a.lam = lam;
+  a.lam_out = lam_out;
+  a.k = k;
+  a.gk = gk;
+  for (int t = 0; t < 4; ++t) a.u[t] = t < depth ? u[t] : nullptr;
+  a.nx = nx;
+  a.ny = ny;
+  a.dt = dt;
+  a.hdt = 0.5f * dt;
+  a.bc = bc;
+  a.chunk_rows = chunk_rows;
+  const int ow = strip_out_width(4);  // HALO = 4 for every depth 1..4
+  a.n_strips = (nx + ow - 1) / ow;
+  const long long items = (long long)a.n_strips * ((ny + chunk_rows - 1) / chunk_rows);
+  if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
+  a.n_items = (int)items;
+  const unsigned blocks = (unsigned)((items + ADJ_TB_WARPS - 1) / ADJ_TB_WARPS);
+  const size_t shm = adjoint_pass_smem(depth);
+  cudaError_t e = ensure_smem_optin_adj(depth, shm);
+  if (e != cudaSuccess) return e;
+  (void)cudaGetLastError();
+  switch (depth) {
+    case 1: adjoint_pass<1><<<blocks, 32 * ADJ_TB_WARPS, shm, s>>>(a); break;
+    case 2: adjoint_pass<2><<<blocks, 32 * ADJ_TB_WARPS, shm, s>>>(a); break;
+    case 3: adjoint_pass<3><<<blocks, 32 * ADJ_TB_WARPS, shm, s>>>(a); break;
+    default: adjoint_pass<4><<<blocks, 32 * ADJ_TB_WARPS, shm, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u, const float* k,
                                 float* gk, int nx, int ny, float dt, int bc, cudaStream_t s) {

@@ -243,22 +243,6 @@ constexpr int VR = 8;  // ring slots
 
 __host__ __device__ constexpr int vring_slot_floats(int by) { return (3 * by + 4) * 128 + 4 * by; }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // Copy the 4 cells x0 .. x0+3 of row (y, z) of u and kappa (and s when
 // with_s) into a slot row under the boundary rule.
 __device__ __forceinline__ void ring_row(const VolArgs& a, int x0, int y, int z, float* du, float* dk,

@@ -105,3 +105,35 @@ def test_adjoint_full_size_differentiation_workload(dev):
     gu, gk = gpu_adjoint(cpb.lib(fma=True), g, dev, g.steps, g.extras["ckpt"], g.bc, uT - tgt)
     assert rel_l2(gu, gu_ref) <= 1e-4
     assert rel_l2(gk, gk_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("bc", [W.DIRICHLET, W.PERIODIC])
+@pytest.mark.parametrize("nx,ny,steps,ckpt", [(256, 130, 37, 20), (520, 77, 10, 10), (128, 40, 7, 3),
+                                              (384, 9, 13, 13)])
+def test_blocked_adjoint_passes_equal_one_step_launches(dev, bc, nx, ny, steps, ckpt):
+    # Where every field allows 16-byte rows the backward sweep runs passes of
+    # up to 4 steps; a gradient buffer off the 16-byte grid makes it launch one
+    # step at a time.  The pass adds each row's gradient terms in step order,
+    # so both give the same bits (--fmad=false build), for every depth the
+    # segment lengths produce (4, and the remainders 3, 2, 1).
+    L = cpb.lib(fma=False)
+    g = W.differentiation(seed=nx + steps, n=nx, ny=ny, steps=steps, ckpt=ckpt)
+    rng = np.random.default_rng(1)
+    lam = torch.from_numpy(rng.standard_normal(g.u.shape).astype(np.float32)).to(dev)
+    u0 = torch.from_numpy(g.u).to(dev)
+    k = torch.from_numpy(g.kappa).to(dev)
+    s = torch.from_numpy((rng.random(g.u.shape, dtype=np.float32) * np.float32(1e-3))).to(dev)
+    wsb = L.cpb_adjoint_workspace_bytes(nx, ny, steps, ckpt)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    n = nx * ny
+    out = []
+    for off in (0, 1):   # gradient buffer 16-byte aligned, then 4 bytes past it
+        gu = torch.empty_like(u0)
+        gk_buf = torch.empty(n + 4, dtype=torch.float32, device=dev)
+        gk = gk_buf[off:off + n]
+        L.cpb_stencil_adjoint(u0, k, s, lam, nx, ny, steps, float(g.dt), bc, ckpt, gu, gk, ws, wsb)
+        torch.cuda.synchronize()
+        out.append((gu.cpu().numpy(), gk.cpu().numpy().reshape(ny, nx)))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert L.cpb_device_status() == 0
