@@ -177,9 +177,11 @@ cpb_status cpb_tuning_load(const char* path, const char* device, int* loaded);
  * cache and return it in *best.  Synchronises `stream`.  The paper leaves the
  * choice of its grain size to heuristics per kernel (Sec. IV "Runtime
  * Optimizations"); this measures instead.  Candidates: depth 1..6 and 8,
- * chunk 64..512 rows, 1..4 warps per CTA, both row-load variants, 2..8 ring
- * stages; each timed twice (the better run counts), the best twelve again
- * four times.  Arguments are validated as for cpb_stencil_launch. */
+ * chunk 16..512 rows, 1..4 warps per CTA, both row-load variants, 2..8 ring
+ * stages, and the built-in default; each timed twice (the better run counts), the best twelve again
+ * four times.  A timed run is an odd number of passes of the candidate's
+ * depth near `steps` steps, repeated to at least about 1 ms.  Arguments are
+ * validated as for cpb_stencil_launch. */
 cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src, int nx, int ny,
                         int steps, float dt, cpb_boundary bc, cpb_dtype dtype, cpb_stream_t stream,
                         cpb_tuning* best);

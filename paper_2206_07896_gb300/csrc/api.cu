@@ -555,7 +555,8 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
   if (st != CPB_SUCCESS) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int ks[] = {1, 2, 3, 4, 5, 6, 8};
-  const int chunks[] = {64, 96, 128, 192, 256, 512};
+  // short chunks give small grids a full wave of warp items
+  const int chunks[] = {16, 32, 64, 96, 128, 192, 256, 512};
   const int wpbs[] = {1, 2, 4};
   const int variants[] = {0, 1};
   const int stages_list[] = {2, 4, 8};
@@ -563,16 +564,24 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
   CPB_TRY(cudaEventCreate(&e0));
   CPB_TRY(cudaEventCreate(&e1));
   const int probe = steps >= 1 ? steps : 16;
-  // Time `reps` runs of a probe (a multiple of k near `probe` steps, so every
-  // pass has depth k) after one warm-up run; returns cell updates per second.
+  // Time `reps` runs of a probe after one timed warm-up run; returns cell
+  // updates per second.  The probe is an odd number of passes of depth k
+  // near `probe` steps, so every pass has depth k (an even count would split
+  // one pass in two); a run shorter than 1 ms is repeated until the timed
+  // region reaches about 1 ms, so small grids are not timed on noise.
+  auto time_runs = [&](const cpb_tuning& t, int n, int reps, float* ms) -> bool {
+    if (cudaEventRecord(e0, s) != cudaSuccess) return false;
+    for (int rep = 0; rep < reps; ++rep)
+      if (enqueue_tuned(f, nx, ny, n, dt, bc, dtype, t, s) != CPB_SUCCESS) return false;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return false;
+    return cudaEventElapsedTime(ms, e0, e1) == cudaSuccess && *ms > 0.0f;
+  };
   auto rate_of = [&](const cpb_tuning& t, int reps) -> double {
-    const int n = std::max(t.k, (probe / t.k) * t.k);
-    if (enqueue_tuned(f, nx, ny, n, dt, bc, dtype, t, s) != CPB_SUCCESS) return -1.0;
-    if (cudaEventRecord(e0, s) != cudaSuccess) return -1.0;
-    for (int rep = 0; rep < reps; ++rep) enqueue_tuned(f, nx, ny, n, dt, bc, dtype, t, s);
-    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+    const int n = t.k * (std::max(1, probe / t.k) | 1);
     float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.0f) return -1.0;
+    if (!time_runs(t, n, 1, &ms)) return -1.0;  // warm-up, and the length of one run
+    reps = std::max(reps, std::min(64, (int)std::ceil(1.0f / ms)));
+    if (!time_runs(t, n, reps, &ms)) return -1.0;
     return (double)reps * n * (double)nx * ny / (ms * 1e-3);
   };
   // Phase 1: screen every candidate (the better of two single runs, so one
@@ -591,6 +600,11 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
             const double r = std::max(rate_of(t, 1), rate_of(t, 1));
             if (r > 0.0) screened.push_back({r, t});
           }
+  {  // the built-in default (its chunk height is sized for one wave) competes too
+    const cpb_tuning t = default_tuning(nx, ny, dtype);
+    const double r = std::max(rate_of(t, 1), rate_of(t, 1));
+    if (r > 0.0) screened.push_back({r, t});
+  }
   std::sort(screened.begin(), screened.end(),
             [](const std::pair<double, cpb_tuning>& x, const std::pair<double, cpb_tuning>& y) {
               return x.first > y.first;
