@@ -225,3 +225,51 @@ def test_batch_autotune_picks_a_measured_plan_that_stays_exact(dev):
     for g, o in zip(grids, off):
         ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, bc, "f32")
         np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref)
+
+
+@pytest.mark.slow
+def test_full_batching_workload_sampled_grids_bit_exact(dev):
+    # The batching workload as the benchmark runs it: all 4096 grids packed
+    # back to back (each start on a 16-byte boundary), the grain / CTA-size
+    # plan chosen by the batched autotuner, one persistent launch.  Sampled
+    # grids (the most expensive, the cheapest, the widest, the narrowest and a
+    # seeded spread) equal the FP32 oracle bit for bit (--fmad=false build).
+    L = cpb.lib(fma=False)
+    bt = W.batching()
+    cells = bt.nx.astype(np.int64) * bt.ny.astype(np.int64)
+    off = np.zeros(bt.ngrids, np.int64)
+    off[1:] = np.cumsum((cells + 3) // 4 * 4)[:-1]
+    total = int(off[-1] + cells[-1])
+    u = torch.zeros(total, dtype=torch.float32, device=dev)
+    k = torch.ones(total, dtype=torch.float32, device=dev)
+    s = torch.zeros(total, dtype=torch.float32, device=dev)
+    for g in range(bt.ngrids):
+        o, c, b = int(off[g]), int(cells[g]), int(bt.offset[g])
+        u[o:o + c] = torch.from_numpy(bt.u[b:b + c])
+        k[o:o + c] = torch.from_numpy(bt.kappa[b:b + c])
+        s[o:o + c] = torch.from_numpy(bt.src[b:b + c])
+    tu, to = u.clone(), torch.empty_like(u)
+    descs = cpb.batch_descriptors(tu, to, k, s, off, bt.nx, bt.ny, bt.steps, bt.dt)
+    plan = L.cpb_batch_plan_default()
+    order, n_large = L.cpb_batch_order(descs, plan)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    d_order = cpb.to_device_bytes((C.c_int * len(order))(*order), dev)
+    work = torch.zeros(4, dtype=torch.int32, device=dev)
+    plan, _ = L.cpb_batch_autotune(d_descs, d_order, bt.ngrids, n_large, cpb.CPB_F32, W.DIRICHLET, work, plan)
+    del tu, to
+    uo = torch.full_like(u, -1.0)
+    uin = u.clone()
+    descs = cpb.batch_descriptors(uin, uo, k, s, off, bt.nx, bt.ny, bt.steps, bt.dt)
+    d_descs = cpb.to_device_bytes(descs, dev)
+    L.cpb_stencil_batched(d_descs, d_order, bt.ngrids, n_large, cpb.CPB_F32, W.DIRICHLET, plan, work)
+    assert L.cpb_batch_status(work) == 0
+    out = uo.cpu().numpy()
+    cost = cells * bt.steps.astype(np.int64)
+    rng = np.random.default_rng(7)
+    sample = set(np.argsort(cost)[-4:]) | set(np.argsort(cost)[:4]) | {int(np.argmax(bt.nx)), int(np.argmin(bt.nx))}
+    sample |= set(int(x) for x in rng.choice(bt.ngrids, 18, replace=False))
+    for gi in sorted(sample):
+        g = bt.grid(int(gi))
+        ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, W.DIRICHLET, "f32", pool=oracle.host_cores())
+        o = int(off[gi])
+        np.testing.assert_array_equal(out[o:o + g.nx * g.ny].reshape(g.ny, g.nx), ref, err_msg=f"grid {gi}")
