@@ -142,9 +142,9 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
       if (bulk && tma_ok) {
         tma_ok = bulk_item<K, false, false>(a, it, lane, sm.ring, sm.bars, sm.face, status);
         if (!tma_ok)  // a wait expired (status set): redo this item without the ring
-          stream_item<K, false, true>(a, it, lane, sm.face);
+          stream_item<K, false, true, false, true, true>(a, it, lane, sm.face);
       } else {
-        stream_item<K, false, true>(a, it, lane, sm.face);
+        stream_item<K, false, true, false, true, true>(a, it, lane, sm.face);
       }
     }
     // This pass's ordinary stores must be visible to the next pass's bulk

@@ -365,6 +365,9 @@ __device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int n
   }
 }
 
+template <int K, bool BF>
+__device__ __forceinline__ bool item_interior(const StreamArgs& a, int item);
+
 // ---------------------------------------------------------------------------
 // variant 0: register prefetch, one row ahead
 // ---------------------------------------------------------------------------
@@ -373,13 +376,16 @@ __device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int n
 // wrote earlier (the batched persistent kernel); otherwise the read-only path.
 // FULL: the pass depth is K (known at compile time, so the per-level depth
 // guards fold away); otherwise the depth a.depth <= K is read at run time.
-template <int K, bool BF, bool COH, bool FULL = false, bool RE = true>
+// INTERIOR: a Dirichlet item that touches no edge (item_interior) runs with
+// the periodic flag, which skips the ghost masks (a run-time branch here, so
+// no second copy of the loop body).
+template <int K, bool BF, bool COH, bool FULL = false, bool RE = true, bool INTERIOR = false>
 __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int lane, float4* face_ring) {
   constexpr int HALO = (K + 3) & ~3;
   constexpr int OW = 128 - 2 * HALO;
   using IO = Io<BF>;
   const int nx = a.nx, ny = a.ny, d = FULL ? K : a.depth;
-  const bool periodic = a.bc == BC_PERIODIC;
+  const bool periodic = a.bc == BC_PERIODIC || (INTERIOR && item_interior<K, BF>(a, item));
   const int strip = item % a.n_strips, chunk = item / a.n_strips;
   const int xo = strip * OW;
   const LaneCols lc = lane_cols(xo - HALO + 4 * lane, nx, periodic);
