@@ -762,16 +762,48 @@ def run_ours(args):
             L.cpb_stencil_host(hu, hk, hs, ho, nx, ny, T, float(g.dt), g.bc, cpb.CPB_F32, hws, wsb,
                                stream=sh)
             rep_s.append(time.perf_counter() - t0)
-        e2e_s = statistics.median(rep_s)
+        sync_s = statistics.median(rep_s)
+        # The pipelined call: each step copies its inputs in and its result
+        # out, on copy streams beside the compute stream, alternating two
+        # workspaces, so a step's transfers overlap its neighbours' compute.
+        hws2 = [hws, torch.empty(wsb, dtype=torch.uint8, device=dev)]
+        ho2 = [ho, torch.empty_like(hu).pin_memory()]
+        s_in, s_c, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        done = [None, None]
+
+        def async_step(i):
+            w = i % 2
+            if done[w] is not None:
+                s_in.wait_event(done[w])   # that workspace's previous problem has been copied out
+            L.cpb_stencil_host_async(hu, hk, hs, ho2[w], nx, ny, T, float(g.dt), g.bc, cpb.CPB_F32, hws2[w], wsb,
+                                     s_in, s_c, s_out)
+            ev = torch.cuda.Event()
+            ev.record(s_out)
+            done[w] = ev
+
+        for i in range(2):
+            async_step(i)
+        torch.cuda.synchronize()
+        n_async = max(args.steps, 5)
+        t0 = time.perf_counter()
+        for i in range(n_async):
+            async_step(i)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / n_async
         if pg:
-            t = torch.tensor([e2e_s], device=dev)
+            t = torch.tensor([e2e_s, sync_s], device=dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            e2e_s, sync_s = float(t[0].item()), float(t[1].item())
         e2e = {"value": updates * world / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 3 * nx * ny * 4, "d2h_bytes_per_step": nx * ny * 4,
-               "ms_per_step": e2e_s * 1e3, "reps": reps, "ms_min": min(rep_s) * 1e3,
-               "ms_max": max(rep_s) * 1e3, "timing": "median of per-call wall times"}
-        del hws
+               "ms_per_step": e2e_s * 1e3, "steps": n_async,
+               "timing": "cpb_stencil_host_async: consecutive steps on copy-in / compute / copy-out streams and "
+                         "two workspaces; wall time of all steps (pinned copies included) / steps",
+               "sync_call": {"value": updates * world / sync_s / 1e9, "ms_per_step": sync_s * 1e3, "reps": reps,
+                             "ms_min": min(rep_s) * 1e3, "ms_max": max(rep_s) * 1e3,
+                             "timing": "cpb_stencil_host (copies in, runs, copies out, synchronises): median "
+                                       "of per-call wall times"}}
+        del hws, hws2
 
     forms = measure_forms(L, cpb, dev, stream) if (args.forms and rank == 0) else None
 

@@ -265,6 +265,25 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
                             cpb_dtype dtype, void* d_workspace, size_t ws_bytes,
                             cpb_stream_t stream);
 
+/* The same run as cpb_stencil_host, enqueued on three streams and returned
+ * from at once, so that consecutive problems overlap their transfers with
+ * each other's compute (the copy engines and the SMs work side by side; on
+ * the GB300 machine a step's 1 GB of transfers costs about 5 ms over the host
+ * link).  h2d: the copies of u0, kappa, src into the workspace; compute
+ * (waits for them): the tuned passes; d2h (waits for those): the copy of the
+ * result to u_out_host.  The streams must be distinct.  The host buffers
+ * must stay valid, and the workspace unused by anything else, until the
+ * d2h stream has passed this call's copy (the caller synchronises d2h, or
+ * records an event on it, before reading u_out_host).  Consecutive calls
+ * that alternate two workspaces overlap; a call on the workspace of an
+ * unfinished earlier call races with it unless the caller orders them.
+ * Host buffers should be pinned (pageable memory makes the copies
+ * synchronous).  Validation and errors as for cpb_stencil_host. */
+cpb_status cpb_stencil_host_async(const void* u0_host, const void* kappa_host, const void* src_host,
+                                  void* u_out_host, int nx, int ny, int steps, float dt, cpb_boundary bc,
+                                  cpb_dtype dtype, void* d_workspace, size_t ws_bytes, cpb_stream_t h2d,
+                                  cpb_stream_t compute, cpb_stream_t d2h);
+
 /* Shared-memory temporal blocking with the caller's geometry: the
  * multi-barrier kernel class (the paper's srad has nine block
  * synchronisations, Sec. V; its CPU translation needs loop fission with the

@@ -104,6 +104,7 @@ _SIGS = {
     "cpb_bf16k_unpack": (_i, [_vp, _vp, _ll, _vp]),
     "cpb_host_workspace_bytes": (_sz, [_i, _i, _i]),
     "cpb_stencil_host": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _sz, _vp]),
+    "cpb_stencil_host_async": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, _sz, _vp, _vp, _vp]),
     "cpb_batch_plan_default": (_i, [C.POINTER(cpb_batch_plan)]),
     "cpb_batch_order": (_i, [_vp, _i, C.POINTER(cpb_batch_plan), _vp, C.POINTER(_i)]),
     "cpb_batch_work_bytes": (_sz, []),
@@ -297,6 +298,12 @@ class Library:
         self._call("cpb_stencil_host", host_ptr(u0_host), host_ptr(kappa_host), host_ptr(src_host),
                    host_ptr(u_out_host), nx, ny, steps, float(dt), bc, dtype, ptr(d_workspace),
                    ws_bytes, stream_handle(stream))
+
+    def cpb_stencil_host_async(self, u0_host, kappa_host, src_host, u_out_host, nx, ny, steps, dt, bc,
+                               dtype, d_workspace, ws_bytes, h2d, compute, d2h):
+        self._call("cpb_stencil_host_async", host_ptr(u0_host), host_ptr(kappa_host), host_ptr(src_host),
+                   host_ptr(u_out_host), nx, ny, steps, float(dt), bc, dtype, ptr(d_workspace), ws_bytes,
+                   stream_handle(h2d), stream_handle(compute), stream_handle(d2h))
 
     def cpb_batch_plan_default(self) -> dict:
         p = cpb_batch_plan()

@@ -730,6 +730,52 @@ cpb_status cpb_stencil_host(const void* u0_host, const void* kappa_host, const v
   return CPB_SUCCESS;
 }
 
+cpb_status cpb_stencil_host_async(const void* u0_host, const void* kappa_host, const void* src_host,
+                                  void* u_out_host, int nx, int ny, int steps, float dt, cpb_boundary bc,
+                                  cpb_dtype dtype, void* d_workspace, size_t ws_bytes, cpb_stream_t h2d,
+                                  cpb_stream_t compute, cpb_stream_t d2h) {
+  if (!u0_host || !kappa_host || !u_out_host || nx < 1 || ny < 1) return CPB_ERR_INVALID_VALUE;
+  if (!dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
+  if (h2d == compute || compute == d2h || h2d == d2h) return CPB_ERR_INVALID_VALUE;
+  const size_t need = cpb_host_workspace_bytes(nx, ny, dtype);
+  if (!d_workspace || ws_bytes < need || !aligned(d_workspace, 256)) return CPB_ERR_WORKSPACE;
+  const size_t n = (size_t)nx * ny;
+  const size_t ub = n * u_bytes(dtype), kb = n * ks_bytes(dtype);
+  char* base = static_cast<char*>(d_workspace);
+  void* ua = base;
+  void* ubuf = base + align256(ub);
+  void* kd = base + 2 * align256(ub);
+  void* sd = src_host ? base + 2 * align256(ub) + align256(kb) : nullptr;
+  Fields f{ua, ubuf, kd, sd, nullptr};
+  cpb_status st = check_common(f, nx, ny, steps, dt, bc, dtype);
+  if (st != CPB_SUCCESS) return st;
+  cudaStream_t sin = reinterpret_cast<cudaStream_t>(h2d), sc = reinterpret_cast<cudaStream_t>(compute),
+               sout = reinterpret_cast<cudaStream_t>(d2h);
+  // Two events per call, released by cudaEventDestroy once they complete.
+  cudaEvent_t in_done, run_done;
+  CPB_TRY(cudaEventCreateWithFlags(&in_done, cudaEventDisableTiming));
+  const cudaError_t e = cudaEventCreateWithFlags(&run_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(in_done);
+    return from_cuda(e);
+  }
+  auto finish = [&](cpb_status r) {
+    cudaEventDestroy(in_done);
+    cudaEventDestroy(run_done);
+    return r;
+  };
+  cpb_status r = from_cuda(cudaMemcpyAsync(ua, u0_host, ub, cudaMemcpyHostToDevice, sin));
+  if (r == CPB_SUCCESS) r = from_cuda(cudaMemcpyAsync(kd, kappa_host, kb, cudaMemcpyHostToDevice, sin));
+  if (r == CPB_SUCCESS && sd) r = from_cuda(cudaMemcpyAsync(sd, src_host, kb, cudaMemcpyHostToDevice, sin));
+  if (r == CPB_SUCCESS) r = from_cuda(cudaEventRecord(in_done, sin));
+  if (r == CPB_SUCCESS) r = from_cuda(cudaStreamWaitEvent(sc, in_done, 0));
+  if (r == CPB_SUCCESS) r = enqueue_tuned(f, nx, ny, steps, dt, bc, dtype, lookup_tuning(nx, ny, dtype, bc), sc);
+  if (r == CPB_SUCCESS) r = from_cuda(cudaEventRecord(run_done, sc));
+  if (r == CPB_SUCCESS) r = from_cuda(cudaStreamWaitEvent(sout, run_done, 0));
+  if (r == CPB_SUCCESS) r = from_cuda(cudaMemcpyAsync(u_out_host, ubuf, ub, cudaMemcpyDeviceToHost, sout));
+  return finish(r);
+}
+
 cpb_status cpb_batch_plan_default(cpb_batch_plan* plan) {
   if (!plan) return CPB_ERR_INVALID_VALUE;
   plan->grain = 1;

@@ -442,3 +442,33 @@ def test_stream_kernel_equals_warp_level_oracle(dev, exact, bc, k):
     got = run_tuned(exact, g, dev, {"k": k, "chunk_rows": 24, "warps_per_block": 2, "variant": 1,
                                     "stages": 2})
     np.testing.assert_array_equal(got, ref)
+
+
+def test_host_async_calls_overlap_and_stay_exact(dev, exact):
+    # Three problems through the pipelined host call on alternating
+    # workspaces (copy-in, compute and copy-out streams), the third reusing
+    # the first one's workspace once that call's copy-out has passed: every
+    # result equals the oracle bit for bit.
+    grids = [W.random_grid(50 + i, 260, 130, 11 + i, D) for i in range(3)]
+    wsb = exact.cpb_host_workspace_bytes(260, 130, cpb.CPB_F32)
+    ws = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(2)]
+    s_in, s_c, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ins = [tuple(torch.from_numpy(x.copy()).pin_memory() for x in (g.u, g.kappa, g.src)) for g in grids]
+    outs = [torch.empty((130, 260), dtype=torch.float32).pin_memory() for _ in grids]
+    done = [None, None]
+    for i, g in enumerate(grids):
+        w = i % 2
+        if done[w] is not None:
+            s_in.wait_event(done[w])
+        exact.cpb_stencil_host_async(*ins[i], outs[i], g.nx, g.ny, g.steps, float(g.dt), D, cpb.CPB_F32, ws[w],
+                                     wsb, s_in, s_c, s_out)
+        ev = torch.cuda.Event()
+        ev.record(s_out)
+        done[w] = ev
+    torch.cuda.synchronize()
+    for g, o in zip(grids, outs):
+        np.testing.assert_array_equal(o.numpy(), oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, D, "f32"))
+    with pytest.raises(cpb.CpbError) as e:
+        exact.cpb_stencil_host_async(*ins[0], outs[0], 260, 130, 3, float(grids[0].dt), D, cpb.CPB_F32, ws[0], wsb,
+                                     s_in, s_in, s_out)
+    assert e.value.status == cpb.CPB_ERR_INVALID_VALUE
