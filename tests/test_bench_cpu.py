@@ -46,3 +46,19 @@ def test_batch_roofline_per_class_bound():
     # a deeper plan streams fewer bytes for the same updates
     assert bench.batch_roofline(bt, 8, 10.0, sms=152, hbm=6000.0)["classes"]["streamed"]["hbm_bytes"] < \
         cls["streamed"]["hbm_bytes"]
+
+
+def test_stream_roofline_picks_the_binding_bound():
+    sys.path.insert(0, ROOT)
+    import bench
+    cells = 8192 * 8192
+    # depth 8: 14 x 8 operations per cell against 152 x 128 lanes at 2070 MHz
+    # take longer than 16 B per cell at 6671 GB/s: the lanes bind
+    r = bench.stream_roofline(cells, 8, 0.384, 6671.2, 152, 2070.0)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["alu"]["time_bound_us"] - 14 * 8 * cells / (152 * 128 * 2070e6) * 1e6) < 1e-6
+    assert abs(r["frac"] - r["alu"]["time_bound_us"] / 384.0) < 1e-9
+    assert abs(r["hbm"]["frac"] - 16 * cells / 0.384e-3 / 6671.2e9) < 1e-9
+    # depth 1: HBM binds
+    r1 = bench.stream_roofline(cells, 1, 0.168, 6671.2, 152, 2070.0)
+    assert r1["bound"] == "hbm" and r1["unit"] == "GB/s" and r1["frac"] == r1["hbm"]["frac"]
