@@ -191,6 +191,18 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
  * variant-1 kernel gave up; that kernel's output is invalid), and clears it. */
 cpb_status cpb_device_status(int* status);
 
+/* Bounds-checked build (libcpb_check.so: --fmad=false arithmetic plus a range
+ * check on every global element range a kernel reads or writes; the paper
+ * has no counterpart, this stands in for a memory checker).  Synchronises the
+ * device, then returns in *line the source line of the first access found
+ * outside its field since the last call (0: none) and in *unit its
+ * translation unit (1 stream FP32, 2 stream BF16-Kahan, 3 stream BF16-Kahan
+ * per pass, 4 batched, 5 adjoint, 6 3-D, 7 tiled, 8 heat sum; 0: none), and
+ * clears them.  The checked kernel clamped the access into its field, so
+ * nothing outside it was touched, but its result is invalid.  In the other
+ * builds *unit = *line = 0 and the call returns CPB_ERR_UNSUPPORTED_CONFIG. */
+cpb_status cpb_bounds_status(int* unit, int* line);
+
 /* Test hook: mbarrier wait limit in polls (<= 0: default, about 1M polls) and
  * a row index whose TMA copies are withheld (-1: off): its ring slot is told
  * the row's byte count but no copy is issued, so the wait for that slot runs

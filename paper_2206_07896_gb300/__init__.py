@@ -95,6 +95,7 @@ _SIGS = {
     "cpb_tuning_load": (_i, [C.c_char_p, C.c_char_p, C.POINTER(_i)]),
     "cpb_autotune": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _i, _i, _vp, C.POINTER(cpb_tuning)]),
     "cpb_device_status": (_i, [C.POINTER(_i)]),
+    "cpb_bounds_status": (_i, [C.POINTER(_i), C.POINTER(_i)]),
     "cpb_debug_set": (_i, [_i, _i]),
     "cpb_heat_sum_workspace_bytes": (_sz, [_i, _i]),
     "cpb_heat_sum": (_i, [_vp, _i, _i, _i, _vp, _vp, _sz, _vp]),
@@ -268,6 +269,13 @@ class Library:
         self._call("cpb_device_status", C.byref(st))
         return st.value
 
+    def cpb_bounds_status(self):
+        """(unit, line) of the first out-of-range access since the last call,
+        (0, 0) if none; raises CpbError outside the bounds-checked build."""
+        u, ln = _i(), _i()
+        self._call("cpb_bounds_status", C.byref(u), C.byref(ln))
+        return u.value, ln.value
+
     def cpb_debug_set(self, wait_limit, inject_row):
         self._call("cpb_debug_set", wait_limit, inject_row)
 
@@ -430,6 +438,16 @@ def lib(fma: bool = True) -> Library:
     if fma not in _LIBS:
         _LIBS[fma] = Library(_build.lib_path("libcpb.so" if fma else "libcpb_nofma.so"))
     return _LIBS[fma]
+
+
+_CHECKED: list = []
+
+
+def lib_checked() -> Library:
+    """The bounds-checked build (--fmad=false arithmetic, cpb_bounds_status)."""
+    if not _CHECKED:
+        _CHECKED.append(Library(_build.lib_path("libcpb_check.so")))
+    return _CHECKED[0]
 
 
 def _forward(name):

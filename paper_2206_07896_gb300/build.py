@@ -1,10 +1,13 @@
 """Build libcpb for sm_103a, in-tree: paper_2206_07896_gb300/_build/.
 
-Two builds of the same sources:
+Three builds of the same sources:
   libcpb.so        default: the compiler may contract multiply-adds into FMAs.
   libcpb_nofma.so  --fmad=false: every FP32 operation rounds on its own, in
                    the library's defined order (bit-exact against the CPU
                    oracle's FP32 mode).
+  libcpb_check.so  the --fmad=false build with a range check on every global
+                   element range a kernel reads or writes (a debug build in
+                   place of a memory checker; cpb_bounds_status reports).
 Translation units compile in parallel; nvcc links each set into a shared
 object with the CUDA runtime linked statically.
 """
@@ -22,7 +25,8 @@ OUT = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "--expt-relaxed-constexpr"]
-VARIANTS = {"libcpb.so": ["--fmad=true"], "libcpb_nofma.so": ["--fmad=false", "-DCPB_EXACT_ARITH"]}
+VARIANTS = {"libcpb.so": ["--fmad=true"], "libcpb_nofma.so": ["--fmad=false", "-DCPB_EXACT_ARITH"],
+            "libcpb_check.so": ["--fmad=false", "-DCPB_EXACT_ARITH", "-DCPB_BOUNDS_CHECK"]}
 
 
 def nvcc() -> str:

@@ -637,6 +637,30 @@ cpb_status cpb_device_status(int* status) {
   return CPB_SUCCESS;
 }
 
+cpb_status cpb_bounds_status(int* unit, int* line) {
+  if (!unit || !line) return CPB_ERR_INVALID_VALUE;
+  CPB_TRY(cudaDeviceSynchronize());
+  cudaError_t (*const readers[])(int*) = {read_bounds_stream_f32, read_bounds_stream_bf16k,
+                                          read_bounds_stream_bf16k_block, read_bounds_batch,
+                                          read_bounds_adjoint, read_bounds_vol, read_bounds_tile,
+                                          read_bounds_sum};
+  *unit = 0;
+  *line = 0;
+  for (int u = 0; u < (int)(sizeof(readers) / sizeof(readers[0])); ++u) {
+    int l = 0;
+    CPB_TRY(readers[u](&l));
+    if (l != 0 && *line == 0) {
+      *unit = u + 1;
+      *line = l;
+    }
+  }
+#ifdef CPB_BOUNDS_CHECK
+  return CPB_SUCCESS;
+#else
+  return CPB_ERR_UNSUPPORTED_CONFIG;
+#endif
+}
+
 cpb_status cpb_debug_set(int wait_limit, int inject_row) {
   g_wait_limit = wait_limit > 0 ? wait_limit : (1 << 20);
   g_inject_on = inject_row >= 0 ? 1 : 0;

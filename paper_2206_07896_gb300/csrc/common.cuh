@@ -90,6 +90,43 @@ __device__ __forceinline__ uint32_t kahan_round(float v, float& eff) {
   return hi | (cm << 16);
 }
 
+// Bounds-checked build (CPB_BOUNDS_CHECK, the library's third build): every
+// element range [i, i + count) a kernel reads from or writes to a field of n
+// elements passes through CPB_CHK(i, count, n).  Outside the field it
+// records the source line in this translation unit's g_bounds_line (the
+// first one wins) and returns a clamped index, so the access stays inside the
+// field; the other builds return i unchanged and compile no check.
+#ifdef CPB_BOUNDS_CHECK
+static __device__ int g_bounds_line;
+#endif
+__device__ __forceinline__ size_t chk_range(size_t i, size_t count, size_t n, int line) {
+#ifdef CPB_BOUNDS_CHECK
+  if (i > n || count > n - i) {
+    atomicCAS(&g_bounds_line, 0, line);
+    return n >= count ? n - count : 0;
+  }
+#endif
+  (void)count;
+  (void)n;
+  (void)line;
+  return i;
+}
+#define CPB_CHK(i, count, n) ::cpb::chk_range((size_t)(i), (size_t)(count), (size_t)(n), __LINE__)
+
+// Host side: read and clear this translation unit's g_bounds_line (0 in the
+// builds without checks).
+static inline cudaError_t read_bounds_word(int* out) {
+#ifdef CPB_BOUNDS_CHECK
+  const int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_bounds_line, sizeof(int));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(g_bounds_line, &zero, sizeof(int));
+#else
+  *out = 0;
+  return cudaSuccess;
+#endif
+}
+
 // Per-thread asynchronous copies global -> shared (cp.async): 16 or 4 bytes,
 // src_bytes = 0 fills the destination with zeros (the source address must
 // still be a valid one).  One commit group per call of cp_async_commit;

@@ -62,6 +62,17 @@ cudaError_t read_stream_status_f32(int* out);
 cudaError_t read_stream_status_bf16k(int* out);
 cudaError_t read_stream_status_bf16k_block(int* out);
 
+// Read and clear the first out-of-range source line recorded by each
+// translation unit's kernels (bounds-checked build; 0 otherwise).
+cudaError_t read_bounds_stream_f32(int* out);
+cudaError_t read_bounds_stream_bf16k(int* out);
+cudaError_t read_bounds_stream_bf16k_block(int* out);
+cudaError_t read_bounds_batch(int* out);
+cudaError_t read_bounds_adjoint(int* out);
+cudaError_t read_bounds_vol(int* out);
+cudaError_t read_bounds_tile(int* out);
+cudaError_t read_bounds_sum(int* out);
+
 // The shared-memory temporal-blocked tiled kernel (k_tile.cu): d steps per
 // launch, bx x by threads, four (bx + 2d) x (by + 2d) float tiles.
 size_t tile_blocked_smem_bytes(int bx, int by, int d);

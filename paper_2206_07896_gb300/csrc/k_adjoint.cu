@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(ADJ_BX* ADJ_BY)
   const int j = blockIdx.y * ADJ_BY + threadIdx.y;
   if (i >= nx || j >= ny) return;
   const bool periodic = bc == BC_PERIODIC;
-  const size_t c = (size_t)j * nx + i;
+  const size_t n = (size_t)nx * ny;
+  const size_t c = CPB_CHK((size_t)j * nx + i, 1, n);
   const float lc = lam[c], uc = u[c], kc = k[c];
   // neighbour values across the faces W, E, S, N
   float ln[4], un[4], kn[4];
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(ADJ_BX* ADJ_BY)
       inside[f] = ii >= 0 && ii < nx && jj >= 0 && jj < ny;
     }
     if (inside[f]) {
-      const size_t g = (size_t)jj * nx + ii;
+      const size_t g = CPB_CHK((size_t)jj * nx + ii, 1, n);
       ln[f] = lam[g];
       un[f] = u[g];
       kn[f] = k[g];
@@ -103,10 +104,11 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS)
   const bool periodic = bc == BC_PERIODIC;
   const int xv = periodic ? wrap_index(x0, nx) : (x0 < nx ? x0 : nx - 4);  // a valid 16-byte column
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const size_t n = (size_t)nx * ny;
   auto load_row = [&](int r) -> Row3 {
     Row3 R{z4, z4, z4};
     if (periodic || (r >= 0 && r < ny)) {
-      const size_t g = (size_t)(periodic ? wrap_index(r, ny) : r) * nx + xv;
+      const size_t g = CPB_CHK((size_t)(periodic ? wrap_index(r, ny) : r) * nx + xv, 4, n);
       R.l = ldg4(lam, g);
       R.u = ldg4(u, g);
       R.k = ldg4(k, g);
@@ -120,12 +122,12 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS)
   // Row j's gradient accumulator and x-halo values, loaded one row ahead
   // like the rows of lambda, u and kappa, so no load is waited for at its use.
   auto load_gk = [&](int r) -> float4 {
-    return (r < y1 && x0 < nx) ? *reinterpret_cast<const float4*>(gk + (size_t)r * nx + x0) : z4;
+    return (r < y1 && x0 < nx) ? *reinterpret_cast<const float4*>(gk + CPB_CHK((size_t)r * nx + x0, 4, n)) : z4;
   };
   auto load_halo = [&](int r, float& hl, float& hu, float& hk) {
     hl = hu = hk = 0.f;
     if ((lane == 0 || lane == 31) && hin && r < y1) {
-      const size_t g = (size_t)r * nx + xhc;
+      const size_t g = CPB_CHK((size_t)r * nx + xhc, 1, n);
       hl = __ldg(lam + g);
       hu = __ldg(u + g);
       hk = __ldg(k + g);
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS)
     const float uW1 = __shfl_up_sync(0xffffffffu, C.u.w, 1), uE1 = __shfl_down_sync(0xffffffffu, C.u.x, 1);
     const float kW1 = __shfl_up_sync(0xffffffffu, C.k.w, 1), kE1 = __shfl_down_sync(0xffffffffu, C.k.x, 1);
     if (x0 < nx) {
-      const size_t c0 = (size_t)j * nx + x0;
+      const size_t c0 = CPB_CHK((size_t)j * nx + x0, 4, n);
       const float4 g_old = g_cur;
       const bool iS = periodic || j - 1 >= 0, iN = periodic || j + 1 < ny;
       float lo[4], go[4];
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(32 * ADJ_TB_WARPS) adjoint_pass(const AdjPassA
   auto row_of = [&](int r, bool& in) -> size_t {
     in = periodic || (r >= 0 && r < ny);
     const int rr = periodic ? wrap_near(r, ny) : clamp_index(r, ny);
-    return (size_t)rr * nx + lc.xv;
+    return CPB_CHK((size_t)rr * nx + lc.xv, 4, (size_t)nx * ny);
   };
   auto issue = [&](int r, int slot) {
     float4* d = ring + (size_t)slot * (D + 3) * 32;
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(32 * ADJ_TB_WARPS) adjoint_pass(const AdjPassA
     }
     const int ro = r_in - D;
     if (ro >= y0 && lane_out) {
-      const size_t g = (size_t)ro * nx + lc.xs;
+      const size_t g = CPB_CHK((size_t)ro * nx + lc.xs, 4, (size_t)nx * ny);
       *reinterpret_cast<float4*>(a.lam_out + g) = out;
       *reinterpret_cast<float4*>(a.gk + g) = g_out;
     }
@@ -498,5 +500,7 @@ cudaError_t launch_adjoint_step(const float* lam, float* lam_out, const float* u
   adjoint_step<<<grid, block, 0, s>>>(lam, lam_out, u, k, gk, nx, ny, dt, 0.5f * dt, bc);
   return cudaGetLastError();
 }
+
+cudaError_t read_bounds_adjoint(int* out) { return read_bounds_word(out); }
 
 }  // namespace cpb

@@ -103,8 +103,10 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
   const size_t n = (size_t)nx * ny;
   if (S == 0) {
     const int tid = wib * 32 + lane, nt = nw * 32;
-    for (size_t i = tid; i < n; i += nt)
-      static_cast<float*>(g.u_out)[i] = __ldcg(static_cast<const float*>(g.u_in) + i);
+    for (size_t i = tid; i < n; i += nt) {
+      const size_t j = CPB_CHK(i, 1, n);
+      static_cast<float*>(g.u_out)[j] = __ldcg(static_cast<const float*>(g.u_in) + j);
+    }
     team_sync<CTA>();
     return;
   }
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(BatchDepth<K>::MAX_THREADS, 1)
     if (first >= n_large) break;
     const int last = min(first + grain, n_large);
     for (int q = first; q < last; ++q) {
-      const cpb_grid_desc g = descs[order[q]];
+      const cpb_grid_desc g = descs[CPB_CHK(order[q], 1, ngrids)];
       run_grid<K, true>(g, bc, wib, nw, lane, &work[2], sm, tma_ok, dbg);
     }
   }
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(BatchDepth<K>::MAX_THREADS, 1)
     if (first >= n_small) break;
     const int last = min(first + grain, n_small);
     for (int q = first; q < last; ++q) {
-      const cpb_grid_desc g = descs[order[n_large + q]];
+      const cpb_grid_desc g = descs[CPB_CHK(order[n_large + q], 1, ngrids)];
       run_grid<K, false>(g, bc, 0, 1, lane, &work[2], sm, tma_ok, dbg);
     }
   }
@@ -232,5 +234,7 @@ cudaError_t launch_batch(int depth, const cpb_grid_desc* descs, const int* order
     batch_kernel<4><<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, dbg, work);
   return cudaGetLastError();
 }
+
+cudaError_t read_bounds_batch(int* out) { return read_bounds_word(out); }
 
 }  // namespace cpb

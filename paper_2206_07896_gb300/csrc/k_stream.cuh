@@ -339,16 +339,18 @@ struct Pipe {
   }
 };
 
-// Store one output row of a lane (only columns this strip owns).
+// Store one output row of a lane (only columns this strip owns) into a
+// field of n cells.
 template <bool BF>
-__device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int nx, bool vec,
+__device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int nx, size_t n, bool vec,
                                           float4 v, uint4 packed) {
   if (vec) {
     if (xs < nx) {
+      const size_t i = CPB_CHK(row + xs, 4, n);
       if (BF)
-        *reinterpret_cast<uint4*>(static_cast<uint32_t*>(u_out) + row + xs) = packed;
+        *reinterpret_cast<uint4*>(static_cast<uint32_t*>(u_out) + i) = packed;
       else
-        *reinterpret_cast<float4*>(static_cast<float*>(u_out) + row + xs) = v;
+        *reinterpret_cast<float4*>(static_cast<float*>(u_out) + i) = v;
     }
   } else {
     const float vv[4] = {v.x, v.y, v.z, v.w};
@@ -356,10 +358,11 @@ __device__ __forceinline__ void store_row(void* u_out, size_t row, int xs, int n
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (xs + e < nx) {
+        const size_t i = CPB_CHK(row + xs + e, 1, n);
         if (BF)
-          static_cast<uint32_t*>(u_out)[row + xs + e] = pw[e];
+          static_cast<uint32_t*>(u_out)[i] = pw[e];
         else
-          static_cast<float*>(u_out)[row + xs + e] = vv[e];
+          static_cast<float*>(u_out)[i] = vv[e];
       }
     }
   }
@@ -392,21 +395,23 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
   const int y0 = chunk * a.chunk_rows;
   const int y1 = min(y0 + a.chunk_rows, ny);
   const bool lane_out = lane >= HALO / 4 && lane < (HALO + OW) / 4;
+  const size_t ncell = (size_t)nx * ny;
 
   auto load_row = [&](int r, float4& U, float4& Kp, float4& S) {
     bool rin = periodic || (r >= 0 && r < ny);
     int rr = periodic ? wrap_near(r, ny) : clamp_index(r, ny);
     size_t row = (size_t)rr * nx;
     if (a.vec) {
-      float4 k4 = IO::k4(a.kappa, row + lc.xv);
+      const size_t iv = CPB_CHK(row + lc.xv, 4, ncell);
+      float4 k4 = IO::k4(a.kappa, iv);
       if (!periodic) {  // Dirichlet ghost lanes take kappa of the edge cell
         if (lc.kb == 1) k4 = f4(k4.x);
         if (lc.kb == 2) k4 = f4(k4.w);
       }
       Kp = k4;
       if (rin && lc.cin4) {
-        U = COH ? IO::u4_cg(a.u_in, row + lc.xv) : IO::u4(a.u_in, row + lc.xv);
-        S = a.src ? IO::k4(a.src, row + lc.xv) : f4(0.0f);
+        U = COH ? IO::u4_cg(a.u_in, iv) : IO::u4(a.u_in, iv);
+        S = a.src ? IO::k4(a.src, iv) : f4(0.0f);
       } else {
         U = f4(0.0f);
         S = f4(0.0f);
@@ -415,11 +420,11 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
       float uu[4], kk[4], ss[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        kk[e] = IO::k1(a.kappa, row + lc.xe[e]);
+        const size_t ie = CPB_CHK(row + lc.xe[e], 1, ncell);
+        kk[e] = IO::k1(a.kappa, ie);
         bool in = rin && lc.ine[e];
-        uu[e] = in ? (COH ? IO::u1_cg(a.u_in, row + lc.xe[e]) : IO::u1(a.u_in, row + lc.xe[e]))
-                   : 0.0f;
-        ss[e] = (in && a.src) ? IO::k1(a.src, row + lc.xe[e]) : 0.0f;
+        uu[e] = in ? (COH ? IO::u1_cg(a.u_in, ie) : IO::u1(a.u_in, ie)) : 0.0f;
+        ss[e] = (in && a.src) ? IO::k1(a.src, ie) : 0.0f;
       }
       U = make_float4(uu[0], uu[1], uu[2], uu[3]);
       Kp = make_float4(kk[0], kk[1], kk[2], kk[3]);
@@ -440,7 +445,7 @@ __device__ __forceinline__ void stream_item(const StreamArgs& a, int item, int l
     pipe.template step<decltype(parity)::value, FULL>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un, kn,
                                                       sn, out, packed);
     const int ro = r_in - d;
-    if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, a.vec, out, packed);
+    if (ro >= y0 && lane_out) store_row<BF>(a.u_out, (size_t)ro * nx, lc.xs, nx, ncell, a.vec, out, packed);
   };
   int r_in = y0 - d;
   for (; r_in + 1 < r_end; r_in += 2) {  // unrolled by 2: register slots alternate by parity
@@ -602,8 +607,8 @@ __device__ __forceinline__ void issue_row(const StreamArgs& a, const CopyPlan& c
   if (lane == 0) mbar_arrive_expect_tx(bar, cp.kappa_bytes + (rin ? cp.us_bytes : 0u));
   if (cp.active && (rin || cp.field == 0) && !withhold) {
     const int rr = periodic ? wrap_near(r, a.ny) : clamp_index(r, a.ny);
-    const size_t g = (size_t)rr * a.nx + cp.col;
     const size_t eb = cp.field == 1 ? Io<BF>::U_BYTES : Io<BF>::KS_BYTES;
+    const size_t g = CPB_CHK((size_t)rr * a.nx + cp.col, cp.bytes / eb, (size_t)a.nx * a.ny);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     bulk_g2s(slot + cp.dst_off, cp.src_base + g * eb, cp.bytes, bar);
   }
@@ -672,6 +677,7 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
   const int y1 = min(y0 + a.chunk_rows, ny);
   // Lanes that store: inside the strip's output columns and the grid.
   const bool lane_store = lane >= HALO / 4 && lane < (HALO + OW) / 4 && lc.xs < nx;
+  const size_t ncell = (size_t)nx * ny;
   const int r_first = y0 - d, r_end = y1 + d, nrows = r_end - r_first;
   // Slot offsets (cells) of this lane's 4 cells and of the edge access that
   // supplies kappa to a Dirichlet ghost lane.
@@ -735,8 +741,13 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
       const uint32_t bar = bars_s + 8u * slot;
       if (lane == 0) mbar_arrive_expect_tx(bar, tx_periodic);
       if (cp.active && i != inject_i) {
+        const unsigned char* src = next_src;
+#ifdef CPB_BOUNDS_CHECK
+        const size_t eb = cp.field == 1 ? SL::UB : SL::KB;
+        src = cp.src_base + CPB_CHK((size_t)(next_src - cp.src_base) / eb, cp.bytes / eb, (size_t)nx * ny) * eb;
+#endif
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_g2s(ring_s + (uint32_t)(slot * SL::BYTES + cp.dst_off), next_src, cp.bytes, bar);
+        bulk_g2s(ring_s + (uint32_t)(slot * SL::BYTES + cp.dst_off), src, cp.bytes, bar);
       }
       next_src += row_bytes;
       if (++next_row == ny) {
@@ -757,13 +768,13 @@ __device__ __forceinline__ bool bulk_item_bc(const StreamArgs& a, int item, int 
     pipe.template step<decltype(parity)::value, FULL, SLOT>(r_in, d, ny, periodic, lc, a.dt, a.hdt, un,
                                                             kn, sn, out, packed);
     if (i >= 2 * d && lane_store)  // output row r_in - d >= y0
-      store_row<BF>(a.u_out, (size_t)(r_in - d) * nx, lc.xs, nx, true, out, packed);
+      store_row<BF>(a.u_out, (size_t)(r_in - d) * nx, lc.xs, nx, ncell, true, out, packed);
     if constexpr (LV) {  // also the rows of levels 1..d-1 that fall in this chunk
 #pragma unroll
       for (int t = 1; t < K; ++t) {
         const int rho = r_in - t;
         if (t < d && rho >= y0 && rho < y1 && lane_store)
-          store_row<BF>(lv->p[t - 1], (size_t)rho * nx, lc.xs, nx, true,
+          store_row<BF>(lv->p[t - 1], (size_t)rho * nx, lc.xs, nx, ncell, true,
                         pipe.U[t][decltype(parity)::value], packed);
       }
     }
@@ -1025,7 +1036,7 @@ cudaError_t launch_stream_any(const StreamPass& p, int k, cudaStream_t s) {
 }
 
 // Read and clear this translation unit's device status word.
-inline cudaError_t read_stream_status(int* out) {
+static inline cudaError_t read_stream_status(int* out) {
   int zero = 0;
   cudaError_t e = cudaMemcpyFromSymbol(out, g_stream_status, sizeof(int));
   if (e != cudaSuccess) return e;

@@ -6,4 +6,5 @@ cudaError_t launch_stream_bf16k(const StreamPass& p, int k, cudaStream_t s) {
   return launch_stream_any<true>(p, k, s);
 }
 cudaError_t read_stream_status_bf16k(int* out) { return read_stream_status(out); }
+cudaError_t read_bounds_stream_bf16k(int* out) { return read_bounds_word(out); }
 }  // namespace cpb

@@ -46,16 +46,16 @@ __global__ void __launch_bounds__(SUM_THREADS) heat_partial_f32(const float* __r
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
   const long long nvec = (n - head) / 4;
-  const float4* body = reinterpret_cast<const float4*>(u + head);
   for (long long i = tid; i < nvec; i += nthreads) {
-    float4 v = __ldcs(body + i);
+    const size_t j = CPB_CHK(head + 4 * i, 4, n);
+    float4 v = __ldcs(reinterpret_cast<const float4*>(u + j));
     acc += (double)v.x;
     acc += (double)v.y;
     acc += (double)v.z;
     acc += (double)v.w;
   }
-  for (long long i = tid; i < head; i += nthreads) acc += (double)u[i];
-  for (long long i = head + 4 * nvec + tid; i < n; i += nthreads) acc += (double)u[i];
+  for (long long i = tid; i < head; i += nthreads) acc += (double)u[CPB_CHK(i, 1, n)];
+  for (long long i = head + 4 * nvec + tid; i < n; i += nthreads) acc += (double)u[CPB_CHK(i, 1, n)];
   acc = block_reduce(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(SUM_THREADS) heat_partial_bf16k(const uint32_t
   double acc = 0.0;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
-  for (long long i = tid; i < n; i += nthreads) acc += cell_value(u, i);
+  for (long long i = tid; i < n; i += nthreads) acc += cell_value(u, CPB_CHK(i, 1, n));
   acc = block_reduce(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -193,5 +193,7 @@ cudaError_t launch_heat_sum_noalloc(const void* u, long long n, int dtype, doubl
   const int nblocks = (int)((n + NOALLOC_CELLS_PER_BLOCK - 1) / NOALLOC_CELLS_PER_BLOCK);
   return launch_heat_sum(u, n, dtype, d_out, partials, nblocks, s);
 }
+
+cudaError_t read_bounds_sum(int* out) { return read_bounds_word(out); }
 
 }  // namespace cpb

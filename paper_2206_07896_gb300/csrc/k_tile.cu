@@ -28,14 +28,15 @@ __device__ __forceinline__ int wrap_tile(int i, int n) {
 __device__ __forceinline__ void stage(const float* __restrict__ u, const float* __restrict__ k,
                                       int nx, int ny, int bc, int gi, int gj, float* su, float* sk,
                                       int slot) {
+  const size_t n = (size_t)nx * ny;
   if (bc == BC_PERIODIC) {
-    size_t g = (size_t)wrap_tile(gj, ny) * nx + wrap_tile(gi, nx);
+    size_t g = CPB_CHK((size_t)wrap_tile(gj, ny) * nx + wrap_tile(gi, nx), 1, n);
     su[slot] = u[g];
     sk[slot] = k[g];
   } else {
     bool inside = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-    su[slot] = inside ? u[(size_t)gj * nx + gi] : 0.0f;
-    sk[slot] = k[(size_t)clamp_index(gj, ny) * nx + clamp_index(gi, nx)];
+    su[slot] = inside ? u[CPB_CHK((size_t)gj * nx + gi, 1, n)] : 0.0f;
+    sk[slot] = k[CPB_CHK((size_t)clamp_index(gj, ny) * nx + clamp_index(gi, nx), 1, n)];
   }
 }
 
@@ -59,7 +60,7 @@ __global__ void tile_step_f32(const float* __restrict__ u, float* __restrict__ u
   // Region 1: update in-grid cells from the tile.
   if (gi < nx && gj < ny) {
     const int c = (ty + 1) * TW + (tx + 1);
-    const size_t g = (size_t)gj * nx + gi;
+    const size_t g = CPB_CHK((size_t)gj * nx + gi, 1, (size_t)nx * ny);
     const float kc = sk[c];
     uo[g] = cell_update(su[c], su[c - 1], su[c + 1], su[c - TW], su[c + TW], kc + sk[c - 1],
                         kc + sk[c + 1], kc + sk[c - TW], kc + sk[c + TW], dt * s[g], hdt);
@@ -97,9 +98,9 @@ __global__ void tile_blocked_f32(const float* __restrict__ u, float* __restrict_
       float sv = 0.0f;
       if (s) {
         if (periodic)
-          sv = s[(size_t)wrap_tile(gj, ny) * nx + wrap_tile(gi, nx)];
+          sv = s[CPB_CHK((size_t)wrap_tile(gj, ny) * nx + wrap_tile(gi, nx), 1, (size_t)nx * ny)];
         else if (gi >= 0 && gi < nx && gj >= 0 && gj < ny)
-          sv = s[(size_t)gj * nx + gi];
+          sv = s[CPB_CHK((size_t)gj * nx + gi, 1, (size_t)nx * ny)];
       }
       st[c] = sv;
     }
@@ -127,7 +128,7 @@ __global__ void tile_blocked_f32(const float* __restrict__ u, float* __restrict_
   // Region d + 1: write the interior.
   const float* a = (d & 1) ? lev1 : lev0;
   const int gi = blockIdx.x * BX + tx, gj = blockIdx.y * BY + ty;
-  if (gi < nx && gj < ny) uo[(size_t)gj * nx + gi] = a[(ty + d) * TW + tx + d];
+  if (gi < nx && gj < ny) uo[CPB_CHK((size_t)gj * nx + gi, 1, (size_t)nx * ny)] = a[(ty + d) * TW + tx + d];
 }
 
 unsigned g_tile_blocked_optin;  // devices on which the shared-memory opt-in was set
@@ -168,5 +169,7 @@ cudaError_t launch_tile_f32(const float* u_in, float* u_out, const float* kappa,
   tile_step_f32<<<grid, block, shm, s>>>(u_in, u_out, kappa, src, nx, ny, dt, 0.5f * dt, bc);
   return cudaGetLastError();
 }
+
+cudaError_t read_bounds_tile(int* out) { return read_bounds_word(out); }
 
 }  // namespace cpb

@@ -49,8 +49,10 @@ struct VolArgs {
 
 #define CPB_FULL_MASK 0xffffffffu
 
-__device__ __forceinline__ size_t vidx(const VolArgs& a, int x, int y, int z) {
-  return ((size_t)z * a.ny + y) * a.nx + x;
+// Index of cell (x, y, z); `count` cells from there are accessed (checked in
+// the bounds-checked build).
+__device__ __forceinline__ size_t vidx(const VolArgs& a, int x, int y, int z, int count = 1) {
+  return CPB_CHK(((size_t)z * a.ny + y) * a.nx + x, count, (size_t)a.nx * a.ny * a.nz);
 }
 
 // u and kappa of one cell under the boundary rule.
@@ -71,14 +73,14 @@ __device__ __forceinline__ void cell_at(const VolArgs& a, int x, int y, int z, f
 __device__ __forceinline__ void row4(const VolArgs& a, int x0, int y, int z, float4& u4, float4& k4) {
   if (a.vec) {
     if (a.bc == BC_PERIODIC) {
-      const size_t g = vidx(a, wrap_index(x0, a.nx), wrap_index(y, a.ny), wrap_index(z, a.nz));
+      const size_t g = vidx(a, wrap_index(x0, a.nx), wrap_index(y, a.ny), wrap_index(z, a.nz), 4);
       u4 = __ldg(reinterpret_cast<const float4*>(a.u + g));
       k4 = __ldg(reinterpret_cast<const float4*>(a.k + g));
     } else {
       // nx % 4 == 0: the 4 cells are all inside or all outside in x
       const bool xin = x0 < a.nx;
       const bool in = xin && y >= 0 && y < a.ny && z >= 0 && z < a.nz;
-      const size_t g = vidx(a, xin ? x0 : a.nx - 4, clamp_index(y, a.ny), clamp_index(z, a.nz));
+      const size_t g = vidx(a, xin ? x0 : a.nx - 4, clamp_index(y, a.ny), clamp_index(z, a.nz), 4);
       k4 = __ldg(reinterpret_cast<const float4*>(a.k + g));
       if (!xin) k4 = make_float4(k4.w, k4.w, k4.w, k4.w);  // ghost columns: kappa of column nx-1
       u4 = in ? __ldg(reinterpret_cast<const float4*>(a.u + g)) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -96,7 +98,7 @@ __device__ __forceinline__ float4 src4(const VolArgs& a, int x0, int y, int z) {
   float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!a.s || y >= a.ny || z >= a.nz) return r;
   if (a.vec) {
-    if (x0 < a.nx) r = __ldg(reinterpret_cast<const float4*>(a.s + vidx(a, x0, y, z)));
+    if (x0 < a.nx) r = __ldg(reinterpret_cast<const float4*>(a.s + vidx(a, x0, y, z, 4)));
   } else {
     if (x0 < a.nx) r.x = __ldg(a.s + vidx(a, x0, y, z));
     if (x0 + 1 < a.nx) r.y = __ldg(a.s + vidx(a, x0 + 1, y, z));
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(256) vol_kernel(const VolArgs a) {
                     dt, hdt);
       o.w = update7(uc.w, uc.z, uEl, uS.w, uN.w, um.w, up.w, kc.w, kc.z, kEl, kS.w, kN.w, km.w, kp.w, sc.w,
                     dt, hdt);
-      float* dst = a.uo + vidx(a, x0, y, z);
+      float* dst = a.uo + vidx(a, x0, y, z, a.vec ? 4 : min(4, a.nx - x0));
       if (a.vec) {
         *reinterpret_cast<float4*>(dst) = o;
       } else {
@@ -250,11 +252,11 @@ __device__ __forceinline__ void ring_row(const VolArgs& a, int x0, int y, int z,
   size_t g, gk;
   bool in = true;
   if (a.bc == BC_PERIODIC) {
-    g = gk = vidx(a, wrap_index(x0, a.nx), wrap_index(y, a.ny), wrap_index(z, a.nz));
+    g = gk = vidx(a, wrap_index(x0, a.nx), wrap_index(y, a.ny), wrap_index(z, a.nz), 4);
   } else {
     const int xc = x0 < a.nx ? x0 : a.nx - 4;
     in = x0 < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz;
-    g = gk = vidx(a, xc, clamp_index(y, a.ny), clamp_index(z, a.nz));
+    g = gk = vidx(a, xc, clamp_index(y, a.ny), clamp_index(z, a.nz), 4);
   }
   cp_async16(du, a.u + g, in ? 16 : 0);
   cp_async16(dk, a.k + gk, 16);
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(256) vol_ring_kernel(const VolArgs a) {
                              make_float2(uN.z, uN.w), make_float2(kN.z, kN.w), make_float2(um.z, um.w),
                              make_float2(km.z, km.w), make_float2(up.z, up.w), make_float2(kp.z, kp.w),
                              make_float2(sc.z, sc.w));
-      *reinterpret_cast<float4*>(a.uo + vidx(a, x0, y, z)) = make_float4(o0.x, o0.y, o1.x, o1.y);
+      *reinterpret_cast<float4*>(a.uo + vidx(a, x0, y, z, 4)) = make_float4(o0.x, o0.y, o1.x, o1.y);
     }
   }
   cp_async_wait<0>();  // no copy may target this CTA's shared memory after it exits
@@ -421,5 +423,7 @@ cudaError_t launch_vol_f32(const float* u_in, float* u_out, const float* kappa, 
   }
   return cudaGetLastError();
 }
+
+cudaError_t read_bounds_vol(int* out) { return read_bounds_word(out); }
 
 }  // namespace cpb
