@@ -88,8 +88,12 @@ def recorded_traffic(tuning, nx, ny):
 
 # FP32 operations per cell-update of the canonical update with the face sums
 # (kc + kn) and dt * s held across the steps of a pass: 4 differences, 4
-# products, 3 sums, hdt * acc, + dt * s, c + (..): 14.
+# products, 3 sums, hdt * acc, + dt * s, c + (..): 14.  This is the
+# algorithmic figure the roofline reports against.  The flux form shares each
+# face flux between its two cells and executes about 10 (FLUX_OPS_PER_UPDATE):
+# the implementation's own lane bound, reported beside it.
 ALG_OPS_PER_UPDATE = 14
+FLUX_OPS_PER_UPDATE = 10
 
 
 def stream_roofline(cells, k, pass_ms, hbm_gbs, sms, mhz):
@@ -118,14 +122,16 @@ def stream_roofline(cells, k, pass_ms, hbm_gbs, sms, mhz):
 
 def time_bounds(cells, k, hbm_gbs, clk):
     """Lower bounds on one pass of depth k over `cells` cells: HBM bytes at the
-    measured copy rate, and FP32 lane operations (10 per cell-update) on all
-    SMs at the sampled SM clock (or the maximum clock if none was sampled)."""
+    measured copy rate, and the flux form's FP32 lane operations
+    (FLUX_OPS_PER_UPDATE per cell-update) on all SMs at the sampled SM clock
+    (or the maximum clock if none was sampled)."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
     t_hbm = 16.0 * cells / (hbm_gbs * 1e9) * 1e6
-    t_fp32 = 10.0 * cells * k / (sms * 128 * mhz * 1e6) * 1e6
-    return {"hbm": t_hbm, "fp32_lanes": t_fp32, "sms": sms, "sm_mhz": mhz}
+    t_fp32 = float(FLUX_OPS_PER_UPDATE) * cells * k / (sms * 128 * mhz * 1e6) * 1e6
+    return {"hbm": t_hbm, "fp32_lanes": t_fp32, "fp32_lanes_ops_per_update": FLUX_OPS_PER_UPDATE,
+            "sms": sms, "sm_mhz": mhz}
 
 
 def dist_env():
@@ -459,10 +465,11 @@ def batch_roofline(bt, depth, ms, sms, hbm, peak_source="measured", onchip_cells
     u, kappa, s and ping-pong partner fit in one SM's 227 KB of shared memory
     (16 B per cell: at most 14336 cells) could run all their steps on chip:
     their fields cross HBM once per run.  Every other grid streams its fields
-    once per pass of the plan's depth.  FP32 lanes: 10 operations per
-    cell-update (flux form) on all SMs at the maximum SM clock."""
+    once per pass of the plan's depth.  FP32 lanes: ALG_OPS_PER_UPDATE
+    operations per cell-update (the figure the single-grid roofline uses) on
+    all SMs at the maximum SM clock."""
     src = peak_source
-    lane_rate = sms * 128 * 2070e6 / 10.0           # cell-updates per second
+    lane_rate = sms * 128 * 2070e6 / float(ALG_OPS_PER_UPDATE)  # cell-updates per second
     cells = bt.nx.astype(np.int64) * bt.ny.astype(np.int64)
     steps = bt.steps.astype(np.int64)
     small = cells <= onchip_cells
@@ -482,7 +489,8 @@ def batch_roofline(bt, depth, ms, sms, hbm, peak_source="measured", onchip_cells
                         "streamed": {"grids": int((~small).sum()), "hbm_bytes": bytes_large,
                                      "updates": upd_large, "t_hbm_ms": bytes_large / (hbm * 1e9) * 1e3,
                                      "t_fp32_lanes_ms": upd_large / lane_rate * 1e3}},
-            "peak": f"{hbm} GB/s ({src}); FP32 lanes {sms} SMs x 128 at 2070 MHz, 10 operations per update",
+            "peak": f"{hbm} GB/s ({src}); FP32 lanes {sms} SMs x 128 at 2070 MHz, "
+                    f"{ALG_OPS_PER_UPDATE} operations per update",
             "depth": depth}
 
 

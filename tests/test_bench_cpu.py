@@ -43,6 +43,9 @@ def test_batch_roofline_per_class_bound():
     want = (max(cls["on_chip"]["t_hbm_ms"], cls["on_chip"]["t_fp32_lanes_ms"])
             + max(cls["streamed"]["t_hbm_ms"], cls["streamed"]["t_fp32_lanes_ms"]))
     assert abs(r["time_bound_ms"] - want) < 1e-9 and abs(r["frac"] - want / 10.0) < 1e-12
+    # the lane time uses the same operations per update as the single-grid roofline
+    lanes = cls["streamed"]["updates"] * bench.ALG_OPS_PER_UPDATE / (152 * 128 * 2070e6) * 1e3
+    assert abs(cls["streamed"]["t_fp32_lanes_ms"] - lanes) < 1e-9
     # a deeper plan streams fewer bytes for the same updates
     assert bench.batch_roofline(bt, 8, 10.0, sms=152, hbm=6000.0)["classes"]["streamed"]["hbm_bytes"] < \
         cls["streamed"]["hbm_bytes"]
