@@ -516,18 +516,38 @@ def form_adjoint(L, cpb, dev, stream):
                                                       g.bc, cpb.CPB_F32, scratch=scr, stream=sh),
                    3, stream)
 
+    lam = torch.empty_like(u0)
+
     def grad():
         L.cpb_adjoint_forward(u0, k, None, nx, ny, T, float(g.dt), g.bc, ck, uT, ws, wsb, stream=sh)
-        lam = uT - tgt
+        with torch.cuda.stream(stream):
+            torch.sub(uT, tgt, out=lam)
         L.cpb_adjoint_backward(k, None, lam, nx, ny, T, float(g.dt), g.bc, ck, gu, gk, ws, wsb,
                                stream=sh)
 
     ms_grad = _time(grad, 3, stream)
+    # The same gradient captured once as a CUDA graph (151 launches: the
+    # forward passes, lambda_T, the recompute and adjoint passes) and replayed.
+    grad()
+    torch.cuda.synchronize()
+    ref = (gu.clone(), gk.clone())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        grad()
+
+    def replay():
+        with torch.cuda.stream(stream):
+            graph.replay()
+
+    ms_graph = _time(replay, 3, stream)
+    same = bool(torch.equal(gu, ref[0]) and torch.equal(gk, ref[1]))
     upd = nx * ny * T
     ndir = 64
     return {"workload": g.name, "tuning": tuning, "forward": {"gcells": upd / ms_fwd / 1e6, "ms": ms_fwd},
             "gradient": {"ms": ms_grad, "gcells_equiv": upd / ms_grad / 1e6,
                          "ratio_to_forward": ms_grad / ms_fwd},
+            "gradient_cuda_graph": {"ms": ms_graph, "ratio_to_forward": ms_graph / ms_fwd,
+                                    "same_bits_as_eager": same},
             "fd_cost_per_direction_ms": 2 * ms_fwd,
             "fd_64_directions_ms": 2 * ndir * ms_fwd,
             "speedup_gradient_vs_fd_64_directions": 2 * ndir * ms_fwd / ms_grad,
