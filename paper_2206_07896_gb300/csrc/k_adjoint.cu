@@ -259,14 +259,27 @@ struct AdjPassArgs {
   int bc, chunk_rows, n_strips, n_items;
 };
 
-__device__ __forceinline__ float4 boundary_term(float dt, float4 uc, float4 lc) {
-  return make_float4(dt * (0.0f - uc.x) * lc.x, dt * (0.0f - uc.y) * lc.y, dt * (0.0f - uc.z) * lc.z,
-                     dt * (0.0f - uc.w) * lc.w);
-}
-
 __device__ __forceinline__ float4 face_term(float hdt, float4 uf, float4 uc, float4 lc, float4 lf) {
   return make_float4(hdt * (uf.x - uc.x) * (lc.x - lf.x), hdt * (uf.y - uc.y) * (lc.y - lf.y),
                      hdt * (uf.z - uc.z) * (lc.z - lf.z), hdt * (uf.w - uc.w) * (lc.w - lf.w));
+}
+
+// The same face terms on packed pairs, for operands that sit in the same
+// columns (north faces): each component rounds exactly as face_term's.
+__device__ __forceinline__ float4 face_term2(float hdt, float4 uf, float4 uc, float4 lc, float4 lf) {
+  const float2 h = make_float2(hdt, hdt);
+  return cat4(mul2(mul2(h, sub2(lo2(uf), lo2(uc))), sub2(lo2(lc), lo2(lf))),
+              mul2(mul2(h, sub2(hi2(uf), hi2(uc))), sub2(hi2(lc), hi2(lf))));
+}
+
+// Dirichlet boundary-face term dt (0 - u_c) lambda_c, on packed pairs.
+__device__ __forceinline__ float4 boundary_term2(float dt, float4 uc, float4 lc) {
+  const float2 d = make_float2(dt, dt), z = make_float2(0.0f, 0.0f);
+  return cat4(mul2(mul2(d, sub2(z, lo2(uc))), lo2(lc)), mul2(mul2(d, sub2(z, hi2(uc))), hi2(lc)));
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return cat4(add2(lo2(a), lo2(b)), add2(hi2(a), hi2(b)));
 }
 
 template <int D>
@@ -363,7 +376,9 @@ __global__ void __launch_bounds__(32 * ADJ_TB_WARPS) adjoint_pass(const AdjPassA
       Urow[t - 1] = uN;
       const float uE3 = __shfl_down_sync(CPB_FULL, uC.x, 1), lE3 = __shfl_down_sync(CPB_FULL, lC.x, 1);
       float4 pE = face_term(a.hdt, make_float4(uC.y, uC.z, uC.w, uE3), uC, lC, make_float4(lC.y, lC.z, lC.w, lE3));
-      const float4 bt = boundary_term(a.dt, uC, lC);
+      // Dirichlet boundary faces take dt (0 - u_c) lambda_c instead (selected
+      // without branches, so the levels stay one straight-line block)
+      const float4 bt = boundary_term2(a.dt, uC, lC);
       pE.x = bE[0] ? bt.x : pE.x;
       pE.y = bE[1] ? bt.y : pE.y;
       pE.z = bE[2] ? bt.z : pE.z;
@@ -372,25 +387,24 @@ __global__ void __launch_bounds__(32 * ADJ_TB_WARPS) adjoint_pass(const AdjPassA
       // cell: the last of the lane to the west)
       const float pW0 = __shfl_up_sync(CPB_FULL, pE.w, 1);
       const float4 pW = make_float4(bW0 ? bt.x : pW0, pE.x, pE.y, pE.z);
-      float4 pN = face_term(a.hdt, uN, uC, lC, lN);
+      // north faces: same columns, so on packed pairs
+      float4 pN = face_term2(a.hdt, uN, uC, lC, lN);
       if (!periodic && rho + 1 >= ny) pN = bt;
       float4 pS = PN[t - 1];
       if (!periodic && rho - 1 < 0) pS = bt;
       PN[t - 1] = pN;
-      c[t - 1] = make_float4((pW.x + pE.x) + (pS.x + pN.x), (pW.y + pE.y) + (pS.y + pN.y),
-                             (pW.z + pE.z) + (pS.z + pN.z), (pW.w + pE.w) + (pS.w + pN.w));
+      const float4 we = make_float4(pW.x + pE.x, pW.y + pE.y, pW.z + pE.z, pW.w + pE.w);
+      c[t - 1] = add4(we, add4(pS, pN));
     }
     // accumulate: the row at level D leaves, the others move up one level
     float4 g_out;
     if constexpr (D == 1) {
-      g_out = make_float4(g_init.x + c[0].x, g_init.y + c[0].y, g_init.z + c[0].z, g_init.w + c[0].w);
+      g_out = add4(g_init, c[0]);
     } else {
-      g_out = make_float4(A[D - 2].x + c[D - 1].x, A[D - 2].y + c[D - 1].y, A[D - 2].z + c[D - 1].z,
-                          A[D - 2].w + c[D - 1].w);
+      g_out = add4(A[D - 2], c[D - 1]);
 #pragma unroll
-      for (int t = D - 2; t >= 1; --t)
-        A[t] = make_float4(A[t - 1].x + c[t].x, A[t - 1].y + c[t].y, A[t - 1].z + c[t].z, A[t - 1].w + c[t].w);
-      A[0] = make_float4(g_init.x + c[0].x, g_init.y + c[0].y, g_init.z + c[0].z, g_init.w + c[0].w);
+      for (int t = D - 2; t >= 1; --t) A[t] = add4(A[t - 1], c[t]);
+      A[0] = add4(g_init, c[0]);
     }
     const int ro = r_in - D;
     if (ro >= y0 && lane_out) {
