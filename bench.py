@@ -399,6 +399,32 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     # run below uses the fastest plan (each run starts from a fresh copy of u).
     plan, sweep = L.cpb_batch_autotune(d_descs, d_order, bt.ngrids, n_large, cpb.CPB_F32, W.DIRICHLET,
                                        work, plan, stream=sh)
+    # Team shapes at the tuned depth, grain and CTA size: grids of at least
+    # team_cells cells on a whole CTA, the others on teams of team_warps
+    # warps once the CTA's large grids are done.  Each shape re-orders the
+    # queue; the fastest (or the tuned plan as it is) is kept.
+    ms_copy0 = _time(lambda: uin.copy_(u), 3, stream)
+
+    def time_plan(p, d_ord, nl):
+        def run():
+            uin.copy_(u)
+            L.cpb_stencil_batched(d_descs, d_ord, bt.ngrids, nl, cpb.CPB_F32, W.DIRICHLET, p, work, stream=sh)
+        return _time(run, 2, stream) - ms_copy0
+
+    team_ms = {f"team_cells{plan['team_cells']}_team_warps{plan['team_warps']}": time_plan(plan, d_order, n_large)}
+    best_ms = next(iter(team_ms.values()))
+    for tc in (65536, 131072, 262144, 524288):
+        for tw in (2, 3, 4, 6):
+            if (plan["threads"] // 32) % tw:
+                continue
+            p2 = dict(plan, team_cells=tc, team_warps=tw)
+            o2, nl2 = L.cpb_batch_order(descs, p2)
+            d_o2 = cpb.to_device_bytes((C.c_int * len(o2))(*o2), dev)
+            ms2 = time_plan(p2, d_o2, nl2)
+            team_ms[f"team_cells{tc}_team_warps{tw}"] = ms2
+            if ms2 < best_ms:
+                best_ms, plan, d_order, n_large = ms2, p2, d_o2, nl2
+    assert L.cpb_batch_status(work, stream=sh) == 0
 
     def run_batch():
         uin.copy_(u)
@@ -423,7 +449,11 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     with torch.cuda.graph(graph, stream=cap):
         L.cpb_stencil_batched(d_descs, d_order, bt.ngrids, n_large, cpb.CPB_F32, W.DIRICHLET, plan, work,
                               stream=cap)
-    ms_graph = _time(graph.replay, 3, stream)
+    def replay():
+        with torch.cuda.stream(stream):  # on the timed stream, whatever stream is current
+            graph.replay()
+
+    ms_graph = _time(replay, 3, stream)
     status_graph = L.cpb_batch_status(work, stream=sh)
     del graph
     hbm, hsrc = peaks()
@@ -445,6 +475,7 @@ def form_batched(L, cpb, dev, stream, ngrids=4096):
     return {"workload": f"batch-{bt.ngrids}-grids-32..1024-steps-10..500", "updates": upd,
             "cells": int(cells.sum()), "n_large": n_large, "plan": plan,
             "grain_sweep_ms": {f"depth{d}_grain{g}_threads{t}": v for (d, g, t), v in sweep.items()},
+            "team_sweep_ms": team_ms,
             "batched": {"gcells": upd / ms_b / 1e6, "ms": ms_b, "status": status,
                         "timing": "bare launch, u_in restored before each (copy time subtracted)"},
             "batched_cuda_graph": {"gcells": upd / ms_graph / 1e6, "ms": ms_graph, "status": status_graph,

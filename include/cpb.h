@@ -348,7 +348,8 @@ cpb_status cpb_stencil3d_launch(void* u_in, void* u_out, const void* kappa, cons
  * Resident CTAs fetch grids from a device work queue, `grain` grids per atomic
  * fetch (the GPU counterpart of the paper's task queue with block_per_fetch,
  * Sec. IV "Fetch task queue" and "Runtime Optimizations").  Grids with at
- * least team_cells cells run on a whole CTA, smaller ones on one warp.
+ * least team_cells cells run on a whole CTA, smaller ones on teams of
+ * plan->team_warps warps (one warp by default).
  * Each grid's result is written to its u_out; its u_in is clobbered (used as
  * the ping-pong buffer).  Every grid advances plan->depth (4 or 8) time
  * steps per pass; at depth 8 the row loop takes rows in pairs, as in the
@@ -387,6 +388,10 @@ typedef struct {
   int threads;    /* threads per CTA, a multiple of 32, <= 384 at depth 4, <= 256 at depth 8 */
   int team_cells; /* grids with nx*ny >= team_cells run on a whole CTA */
   int depth;      /* time steps per pass over a grid: 4 or 8 */
+  int team_warps; /* warps per team for the other grids: <= 1 one warp per grid;
+                     otherwise a divisor of threads / 32 with at most 15 teams
+                     per CTA, the teams of a CTA taking grids independently
+                     once the whole-CTA grids are done */
 } cpb_batch_plan;
 
 cpb_status cpb_batch_plan_default(cpb_batch_plan* plan);

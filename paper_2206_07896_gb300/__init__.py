@@ -62,7 +62,7 @@ BATCH_TUNE_CANDIDATES = len(BATCH_TUNE_DEPTHS) * len(BATCH_TUNE_GRAINS) * len(BA
 
 class cpb_batch_plan(C.Structure):
     _fields_ = [("grain", C.c_int), ("blocks", C.c_int), ("threads", C.c_int),
-                ("team_cells", C.c_int), ("depth", C.c_int)]
+                ("team_cells", C.c_int), ("depth", C.c_int), ("team_warps", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -427,7 +427,7 @@ def as_plan(p) -> cpb_batch_plan:
     d.update(p)
     d.setdefault("threads", 384 if int(d["depth"]) <= 4 else 256)
     return cpb_batch_plan(int(d["grain"]), int(d["blocks"]), int(d["threads"]), int(d["team_cells"]),
-                          int(d.get("depth", 4)))
+                          int(d.get("depth", 4)), int(d.get("team_warps", 1)))
 
 
 _LIBS: dict[bool, Library] = {}

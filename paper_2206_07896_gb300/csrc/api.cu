@@ -810,6 +810,7 @@ cpb_status cpb_batch_plan_default(cpb_batch_plan* plan) {
   // to 32 x 32 beats one warp per small grid (a long small grid on one warp
   // becomes the critical path): 154 ms at 1024 vs 231 ms at 65536.
   plan->team_cells = 1024;
+  plan->team_warps = 1;
   return CPB_SUCCESS;
 }
 
@@ -823,7 +824,7 @@ bool host_desc_ok(const cpb_grid_desc& g) {
 
 bool plan_ok(const cpb_batch_plan& p) {
   return p.grain >= 1 && p.threads >= 32 && p.threads % 32 == 0 && batch_threads_max(p.depth) > 0 &&
-         p.threads <= batch_threads_max(p.depth) && p.team_cells >= 1;
+         p.threads <= batch_threads_max(p.depth) && p.team_cells >= 1 && batch_team_ok(p.threads, p.team_warps);
 }
 }  // namespace
 
@@ -872,7 +873,7 @@ cpb_status cpb_stencil_batched(const cpb_grid_desc* d_descs, const int* d_order,
   }
   const BatchDebug dbg{g_wait_limit, g_inject_on, g_inject_row};
   return from_cuda(launch_batch(p.depth, d_descs, d_order, ngrids, n_large, (int)bc, p.grain, blocks, p.threads,
-                                dbg, d_work, reinterpret_cast<cudaStream_t>(stream)));
+                                p.team_warps, dbg, d_work, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 cpb_status cpb_batch_status(const int* d_work, int* status, cpb_stream_t stream) {

@@ -110,8 +110,11 @@ struct BatchDebug {
   int inject_on;
   int inject_row;
 };
+// Multi-warp teams for the small-grid queue: team_warps <= 1 (one warp per
+// grid) or a divisor of the CTA's warps with at most 15 teams per CTA.
+bool batch_team_ok(int threads, int team_warps);
 cudaError_t launch_batch(int depth, const cpb_grid_desc* descs, const int* order, int ngrids, int n_large, int bc,
-                         int grain, int blocks, int threads, const BatchDebug& dbg, int* work,
+                         int grain, int blocks, int threads, int team_warps, const BatchDebug& dbg, int* work,
                          cudaStream_t s);
 }  // namespace cpb
 

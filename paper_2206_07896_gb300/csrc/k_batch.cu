@@ -24,6 +24,7 @@ namespace cpb {
 namespace {
 
 constexpr int BATCH_STAGES = 2;  // TMA ring slots per warp
+constexpr int BATCH_MAX_TEAMS = 15;  // named barriers 1..15 for multi-warp teams
 
 // Temporal depths the batched kernel is built for, and the largest CTA of
 // each: one CTA per SM, and the registers of depth 8 (rows in pairs) allow
@@ -81,20 +82,32 @@ __device__ __forceinline__ int team_chunk_rows(int ny, int strips, int nw, int d
   return best;
 }
 
-template <bool CTA>
-__device__ __forceinline__ void team_sync() {
-  if (CTA)
+// A team of warps that works on one grid at a time: the whole CTA (bar 0,
+// __syncthreads), one warp (__syncwarp), or `threads / 32` consecutive warps
+// of a CTA that meet at named barrier `bar` (1 + the team's index).  Every
+// warp of a team takes the same path through a grid, so each barrier is
+// reached by exactly `threads` threads.
+struct Team {
+  int bar;
+  int threads;
+};
+
+__device__ __forceinline__ void team_sync(const Team& t) {
+  if (t.threads == 32)
+    __syncwarp();
+  else if (t.bar == 0)
     __syncthreads();
   else
-    __syncwarp();
+    asm volatile("bar.sync %0, %1;" ::"r"(t.bar), "r"(t.threads) : "memory");
 }
 
-// Run all steps of one grid with a team: the whole CTA (CTA = true) or one warp.
-// sm: this warp's row ring, mbarriers and face ring; tma_ok: the warp's ring
-// is usable (cleared for the rest of the launch if a bounded wait expired).
-template <int K, bool CTA>
+// Run all steps of one grid with a team of nw warps (wib: this warp's index in
+// the team).  sm: this warp's row ring, mbarriers and face ring; tma_ok: the
+// warp's ring is usable (cleared for the rest of the launch if a bounded wait
+// expired).
+template <int K>
 __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int lane, int* status,
-                         const BulkSmem<K, false>& sm, bool& tma_ok, const BatchDebug& dbg) {
+                         const BulkSmem<K, false>& sm, bool& tma_ok, const BatchDebug& dbg, const Team& team) {
   if (!desc_ok(g)) {
     if (lane == 0 && wib == 0) atomicExch(status, (int)CPB_ERR_INVALID_VALUE);
     return;
@@ -107,7 +120,7 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
       const size_t j = CPB_CHK(i, 1, n);
       static_cast<float*>(g.u_out)[j] = __ldcg(static_cast<const float*>(g.u_in) + j);
     }
-    team_sync<CTA>();
+    team_sync(team);
     return;
   }
   constexpr int HALO = (K + 3) & ~3;
@@ -152,7 +165,7 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
     // This pass's ordinary stores must be visible to the next pass's bulk
     // copies (async proxy) before the team moves on.
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    team_sync<CTA>();
+    team_sync(team);
     src_buf = dst;
   }
 }
@@ -160,9 +173,10 @@ __device__ void run_grid(const cpb_grid_desc& g, int bc, int wib, int nw, int la
 template <int K>
 __global__ void __launch_bounds__(BatchDepth<K>::MAX_THREADS, 1)
     batch_kernel(const cpb_grid_desc* __restrict__ descs, const int* __restrict__ order, int ngrids,
-                 int n_large, int bc, int grain, BatchDebug dbg, int* work) {
+                 int n_large, int bc, int grain, int team_warps, BatchDebug dbg, int* work) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ int s_first;
+  __shared__ int s_team_first[BATCH_MAX_TEAMS];
   extern __shared__ __align__(128) unsigned char smem[];
   // this warp's row ring, mbarriers and ring of per-row face terms (k_stream.cuh)
   const BulkSmem<K, false> sm(smem, wib, nw, BATCH_STAGES);
@@ -177,25 +191,50 @@ __global__ void __launch_bounds__(BatchDepth<K>::MAX_THREADS, 1)
     const int last = min(first + grain, n_large);
     for (int q = first; q < last; ++q) {
       const cpb_grid_desc g = descs[CPB_CHK(order[q], 1, ngrids)];
-      run_grid<K, true>(g, bc, wib, nw, lane, &work[2], sm, tma_ok, dbg);
+      run_grid<K>(g, bc, wib, nw, lane, &work[2], sm, tma_ok, dbg, Team{0, (int)blockDim.x});
     }
   }
-  // Phase 2: small grids, one warp per grid.
+  // Phase 2: small grids, one team of team_warps warps per grid (one warp,
+  // or a few warps meeting at a named barrier; the host checks that the
+  // teams tile the CTA).  A team's first thread fetches from the queue.
   const int n_small = ngrids - n_large;
-  for (;;) {
-    int first = 0;
-    if (lane == 0) first = atomicAdd(&work[1], grain);
-    first = __shfl_sync(0xffffffffu, first, 0);
-    if (first >= n_small) break;
-    const int last = min(first + grain, n_small);
-    for (int q = first; q < last; ++q) {
-      const cpb_grid_desc g = descs[CPB_CHK(order[n_large + q], 1, ngrids)];
-      run_grid<K, false>(g, bc, 0, 1, lane, &work[2], sm, tma_ok, dbg);
+  if (team_warps <= 1) {
+    for (;;) {
+      int first = 0;
+      if (lane == 0) first = atomicAdd(&work[1], grain);
+      first = __shfl_sync(0xffffffffu, first, 0);
+      if (first >= n_small) break;
+      const int last = min(first + grain, n_small);
+      for (int q = first; q < last; ++q) {
+        const cpb_grid_desc g = descs[CPB_CHK(order[n_large + q], 1, ngrids)];
+        run_grid<K>(g, bc, 0, 1, lane, &work[2], sm, tma_ok, dbg, Team{0, 32});
+      }
+    }
+  } else {
+    const int tix = wib / team_warps, twib = wib % team_warps;
+    const Team team{1 + tix, 32 * team_warps};
+    for (;;) {
+      if (twib == 0 && lane == 0) s_team_first[tix] = atomicAdd(&work[1], grain);
+      team_sync(team);
+      const int first = s_team_first[tix];
+      team_sync(team);  // every warp of the team has read it before the next fetch
+      if (first >= n_small) break;
+      const int last = min(first + grain, n_small);
+      for (int q = first; q < last; ++q) {
+        const cpb_grid_desc g = descs[CPB_CHK(order[n_large + q], 1, ngrids)];
+        run_grid<K>(g, bc, twib, team_warps, lane, &work[2], sm, tma_ok, dbg, team);
+      }
     }
   }
 }
 
 }  // namespace
+
+bool batch_team_ok(int threads, int team_warps) {
+  if (team_warps <= 1) return true;
+  const int nw = threads / 32;
+  return team_warps <= nw && nw % team_warps == 0 && nw / team_warps <= BATCH_MAX_TEAMS;
+}
 
 int batch_threads_max(int depth) {
   return depth == 4 ? BatchDepth<4>::MAX_THREADS : (depth == 8 ? BatchDepth<8>::MAX_THREADS : 0);
@@ -219,9 +258,10 @@ cudaError_t batch_blocks_per_sm(int depth, int threads, int* out) {
 }
 
 cudaError_t launch_batch(int depth, const cpb_grid_desc* descs, const int* order, int ngrids, int n_large,
-                         int bc, int grain, int blocks, int threads, const BatchDebug& dbg, int* work,
-                         cudaStream_t s) {
+                         int bc, int grain, int blocks, int threads, int team_warps, const BatchDebug& dbg,
+                         int* work, cudaStream_t s) {
   if (batch_threads_max(depth) == 0 || threads > batch_threads_max(depth)) return cudaErrorInvalidValue;
+  if (!batch_team_ok(threads, team_warps)) return cudaErrorInvalidValue;
   const size_t shm = batch_smem(depth, threads);
   cudaError_t e = ensure_smem_optin(batch_fn(depth), g_batch_attr_done[depth == 8], shm);
   if (e != cudaSuccess) return e;
@@ -229,9 +269,9 @@ cudaError_t launch_batch(int depth, const cpb_grid_desc* descs, const int* order
   e = cudaMemsetAsync(work, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (depth == 8)
-    batch_kernel<8><<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, dbg, work);
+    batch_kernel<8><<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, team_warps, dbg, work);
   else
-    batch_kernel<4><<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, dbg, work);
+    batch_kernel<4><<<blocks, threads, shm, s>>>(descs, order, ngrids, n_large, bc, grain, team_warps, dbg, work);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,13 @@ def test_batch_order_is_host_only_lpt(L):
     assert status(L.cpb_batch_order, descs, None) == INV
     assert status(L.cpb_batch_order, descs, {"grain": 0}) == INV
     assert status(L.cpb_batch_order, descs, {"grain": 1, "depth": 8, "threads": 384}) == INV
+    descs[3].dt = 0.1
+    # multi-warp teams must tile the CTA: a divisor of its warps, at most 15 teams
+    for threads, tw in ((384, 4), (384, 3), (384, 12), (256, 2), (128, 4), (384, 1), (384, 0)):
+        L.cpb_batch_order(descs, {"grain": 1, "threads": threads, "team_warps": tw})
+    for threads, tw in ((384, 5), (384, 13), (256, 3), (128, 8)):
+        assert status(L.cpb_batch_order, descs, {"grain": 1, "threads": threads, "team_warps": tw}) == INV
+    assert L.cpb_batch_plan_default()["team_warps"] == 1
 
 
 def test_slab_rows_match_the_row_split(L):

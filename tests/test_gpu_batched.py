@@ -69,13 +69,18 @@ def run_batch(L, grids, dev, bc, plan, u, k, s, off):
                                   {"grain": 2, "blocks": 0, "threads": 128, "team_cells": 1},
                                   {"grain": 1, "blocks": 0, "threads": 256, "team_cells": 4096, "depth": 8},
                                   {"grain": 2, "blocks": 5, "threads": 128, "team_cells": 20000,
-                                   "depth": 8}])
+                                   "depth": 8},
+                                  {"grain": 1, "blocks": 0, "threads": 384, "team_cells": 20000, "team_warps": 4},
+                                  {"grain": 2, "blocks": 4, "threads": 384, "team_cells": 4096, "team_warps": 3},
+                                  {"grain": 1, "blocks": 0, "threads": 256, "team_cells": 1 << 30, "team_warps": 2,
+                                   "depth": 8},
+                                  {"grain": 1, "blocks": 3, "threads": 384, "team_cells": 1 << 30, "team_warps": 12}])
 def test_batched_bit_exact(dev, bc, plan):
     L = cpb.lib(fma=False)
     grids = small_batch(7 + bc, bc)
     u, k, s, off = pack(grids, dev)
     uo, n_large = run_batch(L, grids, dev, bc, plan, u, k, s, off)
-    assert 0 < n_large < len(grids) or plan["team_cells"] == 1
+    assert 0 < n_large < len(grids) or plan["team_cells"] in (1, 1 << 30)
     out = uo.cpu().numpy()
     for g, o in zip(grids, off):
         ref = oracle.direct(g.u, g.kappa, g.src, g.steps, g.dt, bc, "f32")

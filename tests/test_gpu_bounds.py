@@ -159,7 +159,8 @@ def test_3d_kernels_in_bounds(dev, L, bc):
 
 @pytest.mark.parametrize("bc", [D, P])
 @pytest.mark.parametrize("plan", [{"grain": 1, "threads": 384, "team_cells": 4096},
-                                  {"grain": 2, "threads": 128, "team_cells": 1, "depth": 8}])
+                                  {"grain": 2, "threads": 128, "team_cells": 1, "depth": 8},
+                                  {"grain": 1, "threads": 384, "team_cells": 20000, "team_warps": 4}])
 def test_batched_launch_in_bounds(dev, L, bc, plan):
     grids = small_batch(11 + bc, bc)
     u, k, s, off = pack(grids, dev)
