@@ -549,22 +549,25 @@ def form_adjoint(L, cpb, dev, stream):
 
     lam = torch.empty_like(u0)
 
-    def grad():
-        L.cpb_adjoint_forward(u0, k, None, nx, ny, T, float(g.dt), g.bc, ck, uT, ws, wsb, stream=sh)
-        with torch.cuda.stream(stream):
+    def grad(st=stream):
+        h = st.cuda_stream
+        L.cpb_adjoint_forward(u0, k, None, nx, ny, T, float(g.dt), g.bc, ck, uT, ws, wsb, stream=h)
+        with torch.cuda.stream(st):
             torch.sub(uT, tgt, out=lam)
-        L.cpb_adjoint_backward(k, None, lam, nx, ny, T, float(g.dt), g.bc, ck, gu, gk, ws, wsb,
-                               stream=sh)
+        L.cpb_adjoint_backward(k, None, lam, nx, ny, T, float(g.dt), g.bc, ck, gu, gk, ws, wsb, stream=h)
 
     ms_grad = _time(grad, 3, stream)
     # The same gradient captured once as a CUDA graph (151 launches: the
-    # forward passes, lambda_T, the recompute and adjoint passes) and replayed.
+    # forward passes, lambda_T, the recompute and adjoint passes) on a side
+    # stream (capture needs one that is not the default stream) and replayed
+    # on the timed stream.
     grad()
     torch.cuda.synchronize()
     ref = (gu.clone(), gk.clone())
     graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        grad()
+    cap = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=cap):
+        grad(cap)
 
     def replay():
         with torch.cuda.stream(stream):
