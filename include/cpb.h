@@ -502,7 +502,7 @@ cpb_status cpb_slab_rows(int ny, int world, int rank, int depth, cpb_boundary bc
  * `stream`: device to device, or peer to peer through unified addressing).
  * A side with halo 0 is skipped and its pointer may be NULL.  With one rank
  * and a periodic grid, below and above are the slab itself.  Element size
- * from dtype (4 bytes for every storage format).  The caller orders the
+ * from dtype: the u field (4 bytes for every storage format).  The caller orders the
  * exchange after the neighbours' last step (stream order or events).
  * Validation: nx, n_own >= 1, halos in [0, n_own] and not above the
  * neighbours' own row counts, non-null buffers for non-empty sides; else
@@ -510,6 +510,15 @@ cpb_status cpb_slab_rows(int ny, int world, int rank, int depth, cpb_boundary bc
 cpb_status cpb_slab_exchange(void* slab, int nx, int n_own, int halo_lo, int halo_hi, const void* below,
                              int below_halo_lo, int below_n_own, const void* above, int above_halo_lo,
                              int above_n_own, cpb_dtype dtype, cpb_stream_t stream);
+
+/* The same exchange for a field of any element size, row_bytes = nx x the
+ * element size: the kappa and source fields of the BF16-Kahan formats are
+ * 2-byte fields (row_bytes = 2 nx), every other field 4-byte.  A slab's
+ * kappa and source halos are filled once, before its first step.  Validation
+ * as for cpb_slab_exchange (row_bytes >= 1). */
+cpb_status cpb_slab_exchange_rows(void* slab, size_t row_bytes, int n_own, int halo_lo, int halo_hi,
+                                  const void* below, int below_halo_lo, int below_n_own, const void* above,
+                                  int above_halo_lo, int above_n_own, cpb_stream_t stream);
 
 /* One pass of `steps` (1 <= steps <= min of the non-zero halos, and <= 8)
  * steps over the whole slab buffer (rows_total = halo_lo + n_own + halo_hi)

@@ -127,6 +127,7 @@ _SIGS = {
                               _vp, C.POINTER(_vp)]),
     "cpb_slab_rows": (_i, [_i, _i, _i, _i, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
     "cpb_slab_exchange": (_i, [_vp, _i, _i, _i, _i, _vp, _i, _i, _vp, _i, _i, _i, _vp]),
+    "cpb_slab_exchange_rows": (_i, [_vp, _sz, _i, _i, _i, _vp, _i, _i, _vp, _i, _i, _vp]),
     "cpb_slab_step": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _i, _i, C.POINTER(cpb_tuning), _vp]),
     "cpb_graph_launch": (_i, [_vp, _vp]),
     "cpb_graph_destroy": (_i, [_vp]),
@@ -397,6 +398,11 @@ class Library:
                           above_halo_lo, above_n_own, dtype, stream=None):
         self._call("cpb_slab_exchange", ptr(slab), nx, n_own, halo_lo, halo_hi, ptr(below), below_halo_lo,
                    below_n_own, ptr(above), above_halo_lo, above_n_own, dtype, stream_handle(stream))
+
+    def cpb_slab_exchange_rows(self, slab, row_bytes, n_own, halo_lo, halo_hi, below, below_halo_lo, below_n_own,
+                               above, above_halo_lo, above_n_own, stream=None):
+        self._call("cpb_slab_exchange_rows", ptr(slab), row_bytes, n_own, halo_lo, halo_hi, ptr(below),
+                   below_halo_lo, below_n_own, ptr(above), above_halo_lo, above_n_own, stream_handle(stream))
 
     def cpb_slab_step(self, u_in, u_out, kappa, src, nx, rows_total, halo_lo, halo_hi, steps, dt, bc, dtype,
                       tuning=None, stream=None):

@@ -1151,14 +1151,14 @@ cpb_status cpb_slab_rows(int ny, int world, int rank, int depth, cpb_boundary bc
   return CPB_SUCCESS;
 }
 
-cpb_status cpb_slab_exchange(void* slab, int nx, int n_own, int halo_lo, int halo_hi, const void* below,
-                             int below_halo_lo, int below_n_own, const void* above, int above_halo_lo,
-                             int above_n_own, cpb_dtype dtype, cpb_stream_t stream) {
-  if (!slab || nx < 1 || n_own < 1 || !dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
+cpb_status cpb_slab_exchange_rows(void* slab, size_t row_bytes, int n_own, int halo_lo, int halo_hi,
+                                  const void* below, int below_halo_lo, int below_n_own, const void* above,
+                                  int above_halo_lo, int above_n_own, cpb_stream_t stream) {
+  if (!slab || row_bytes < 1 || n_own < 1) return CPB_ERR_INVALID_VALUE;
   if (halo_lo < 0 || halo_hi < 0 || halo_lo > n_own || halo_hi > n_own) return CPB_ERR_INVALID_VALUE;
   if (halo_lo > 0 && (!below || below_halo_lo < 0 || below_n_own < halo_lo)) return CPB_ERR_INVALID_VALUE;
   if (halo_hi > 0 && (!above || above_halo_lo < 0 || above_n_own < halo_hi)) return CPB_ERR_INVALID_VALUE;
-  const size_t row = (size_t)nx * u_bytes(dtype);
+  const size_t row = row_bytes;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* dst = static_cast<char*>(slab);
   if (halo_lo > 0) {
@@ -1171,6 +1171,14 @@ cpb_status cpb_slab_exchange(void* slab, int nx, int n_own, int halo_lo, int hal
                             cudaMemcpyDefault, s));
   }
   return CPB_SUCCESS;
+}
+
+cpb_status cpb_slab_exchange(void* slab, int nx, int n_own, int halo_lo, int halo_hi, const void* below,
+                             int below_halo_lo, int below_n_own, const void* above, int above_halo_lo,
+                             int above_n_own, cpb_dtype dtype, cpb_stream_t stream) {
+  if (nx < 1 || !dtype_ok(dtype)) return CPB_ERR_INVALID_VALUE;
+  return cpb_slab_exchange_rows(slab, (size_t)nx * u_bytes(dtype), n_own, halo_lo, halo_hi, below, below_halo_lo,
+                                below_n_own, above, above_halo_lo, above_n_own, stream);
 }
 
 cpb_status cpb_slab_step(const void* u_in, void* u_out, const void* kappa, const void* src, int nx,

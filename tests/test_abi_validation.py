@@ -146,6 +146,12 @@ def test_slab_exchange_and_step_validation(L):
     assert status(L.cpb_slab_exchange, X, 64, 10, 2, 2, U, 2, 1, U, 2, 10, F32, stream=0) == INV  # neighbour too small
     assert status(L.cpb_slab_exchange, X, 64, 10, 11, 0, U, 2, 20, None, 0, 0, F32, stream=0) == INV
     assert status(L.cpb_slab_exchange, X, 64, 10, 2, 2, U, 2, 10, U, 2, 10, 9, stream=0) == INV
+    # the exchange by row size: the same checks, and a row of at least one byte
+    assert status(L.cpb_slab_exchange_rows, X, 0, 10, 2, 2, U, 2, 10, U, 2, 10, stream=0) == INV
+    assert status(L.cpb_slab_exchange_rows, None, 128, 10, 2, 2, U, 2, 10, U, 2, 10, stream=0) == INV
+    assert status(L.cpb_slab_exchange_rows, X, 128, 10, 2, 2, U, 2, 1, U, 2, 10, stream=0) == INV
+    assert status(L.cpb_slab_exchange_rows, X, 128, 10, 2, 2, None, 2, 10, U, 2, 10, stream=0) == INV
+    assert status(L.cpb_slab_exchange_rows, X, 128, 10, 11, 0, U, 2, 20, None, 0, 0, stream=0) == INV
     assert status(L.cpb_slab_step, U, O, K, S, 64, 14, 2, 2, 3, 0.1, D, F32, stream=0) == INV      # steps > halo
     assert status(L.cpb_slab_step, U, O, K, S, 64, 14, 2, 2, 0, 0.1, D, F32, stream=0) == INV
     assert status(L.cpb_slab_step, U, O, K, S, 64, 4, 2, 2, 1, 0.1, D, F32, stream=0) == INV       # no own rows
