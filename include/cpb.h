@@ -192,8 +192,10 @@ cpb_status cpb_autotune(void* u_a, void* u_b, const void* kappa, const void* src
 cpb_status cpb_device_status(int* status);
 
 /* Bounds-checked build (libcpb_check.so: --fmad=false arithmetic plus a range
- * check on every global element range a kernel reads or writes; the paper
- * has no counterpart, this stands in for a memory checker).  Synchronises the
+ * check on every global element range the stencil, batched, adjoint, 3-D,
+ * tiled and heat-sum kernels read or write; the element-wise conversion
+ * kernels index i < n directly; the paper has no counterpart, this stands in
+ * for a memory checker).  Synchronises the
  * device, then returns in *line the source line of the first access found
  * outside its field since the last call (0: none) and in *unit its
  * translation unit (1 stream FP32, 2 stream BF16-Kahan, 3 stream BF16-Kahan
